@@ -1,0 +1,22 @@
+"""FP64 CPU oracle for the soft-shadow hot path.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference leg may import this package.  It is
+independent of the CUDA path: it imports nothing from ``paper_2005_06671_gb300``
+and shares no source with it.
+
+* ``oracle.cref`` -- ctypes binding of ``shadow_oracle.c`` (C, FP64, OpenMP):
+  brute force over every sample of every ray, the analytic gradient at the
+  argmin, and the maximum mipmap.
+* ``oracle.mini`` -- an independent NumPy restatement for tiny inputs, used to
+  cross-check the C code.
+
+Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
+(closed forms, Monte-Carlo disc area, brute-force block maxima, finite
+differences, and the C-vs-NumPy cross-check); none is "parity unpinned".
+"""
+from .cref import (build_oracle, disc_light, shadow, ray_costs, sin_elev, grad,
+                   maxmip, num_threads, library_path)
+
+__all__ = ["build_oracle", "disc_light", "shadow", "ray_costs", "sin_elev", "grad",
+           "maxmip", "num_threads", "library_path"]

@@ -1,0 +1,184 @@
+"""ctypes binding of the C oracle (``shadow_oracle.c``).  Test infrastructure only.
+
+``build_oracle()`` compiles the C file with gcc (FP64, IEEE semantics: no
+fast-math, no FMA contraction, so x86 and Arm hosts give the same bits).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "shadow_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PROJ = {"gnomonic": 0, "polar_stereo": 1}
+
+
+def library_path():
+    return _LIB
+
+
+def build_oracle(force=False):
+    """Compile the oracle shared library (idempotent)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build_oracle()
+            lib = ctypes.CDLL(_LIB)
+            d, i32, i64, p = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+            lib.or_disc_light.restype = d
+            lib.or_disc_light.argtypes = [d]
+            lib.or_shadow.restype = None
+            lib.or_shadow.argtypes = [p, i32, i32, i64, d, d, i32, d, d, d, d, d, i32, i64,
+                                      p, p, p, p, p]
+            lib.or_ray_costs.restype = i64
+            lib.or_ray_costs.argtypes = [p, i32, i32, i64, d, d, i32, d, d, d, d, d, d, d,
+                                         p, i64]
+            lib.or_sin_elev.restype = None
+            lib.or_sin_elev.argtypes = [p, i32, i32, i64, d, d, i32, d, d, i32, i64, p, p]
+            lib.or_grad.restype = None
+            lib.or_grad.argtypes = [p, i32, i32, i64, d, d, i32, d, d, d, d, i32, i64, p, p,
+                                    p, p, p, p]
+            lib.or_maxmip.restype = i32
+            lib.or_maxmip.argtypes = [p, i32, i32, i64, p]
+            lib.or_num_threads.restype = i32
+            lib.or_num_threads.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _heights(h):
+    h64 = np.ascontiguousarray(h, dtype=np.float64)
+    assert h64.ndim == 2
+    return h64
+
+
+def _rays(uv, lift):
+    if uv is None:
+        return 0, 0, None, None
+    uv = np.ascontiguousarray(uv, dtype=np.float32).reshape(-1, 2)
+    lift = None if lift is None else np.ascontiguousarray(lift, dtype=np.float32).reshape(-1)
+    return 1, uv.shape[0], uv, lift
+
+
+def num_threads():
+    return int(_load().or_num_threads())
+
+
+def disc_light(d):
+    return float(_load().or_disc_light(float(d)))
+
+
+def shadow(h, g, radius, elev, az, alpha, lmax, step_texels=0.5, proj="gnomonic",
+           uv=None, lift=None):
+    """Brute-force forward.  ``uv=None``: one ray per texel centre (row-major);
+    else ``uv`` [n, 2] float32 texel coordinates with optional ``lift`` [n].
+
+    Returns (light float64 [n], argmin int64 [n] (1-based, -1 none), cost float64 [n]).
+    """
+    lib = _load()
+    h64 = _heights(h)
+    ny, nx = h64.shape
+    mode, n, uv, lift = _rays(uv, lift)
+    nr = nx * ny if mode == 0 else n
+    light = np.empty(nr, np.float64)
+    argmin = np.empty(nr, np.int64)
+    cost = np.empty(nr, np.float64)
+    lib.or_shadow(_ptr(h64), nx, ny, nx, float(g), float(radius), PROJ[proj], float(elev),
+                  float(az), float(alpha), float(lmax), float(step_texels), mode, n,
+                  _ptr(uv), _ptr(lift), _ptr(light), _ptr(argmin), _ptr(cost))
+    return light, argmin, cost
+
+
+def ray_costs(h, g, radius, elev, az, lmax, u, v, lift=0.0, step_texels=0.5,
+              proj="gnomonic"):
+    """Cost of every sample j = 1..J along one ray (NaN where outside the tile)."""
+    lib = _load()
+    h64 = _heights(h)
+    ny, nx = h64.shape
+    J = int(np.floor(lmax / (step_texels * g)))
+    out = np.empty(max(J, 1), np.float64)
+    lib.or_ray_costs(_ptr(h64), nx, ny, nx, float(g), float(radius), PROJ[proj],
+                     float(elev), float(az), float(lmax), float(step_texels), float(u),
+                     float(v), float(lift), _ptr(out), out.size)
+    return out[:J]
+
+
+def sin_elev(h, g, radius, elev, az, proj="gnomonic", uv=None):
+    lib = _load()
+    h64 = _heights(h)
+    ny, nx = h64.shape
+    mode, n, uv, _ = _rays(uv, None)
+    nr = nx * ny if mode == 0 else n
+    out = np.empty(nr, np.float64)
+    lib.or_sin_elev(_ptr(h64), nx, ny, nx, float(g), float(radius), PROJ[proj], float(elev),
+                    float(az), mode, n, _ptr(uv), _ptr(out))
+    return out
+
+
+def grad(h, g, radius, elev, az, alpha, argmin, gL, step_texels=0.5, proj="gnomonic",
+         uv=None, lift=None):
+    """Analytic gradient of sum(gL * light) at the given argmin.
+
+    Returns (grad_h float64 [ny, nx], grad_sun float64 [5] =
+    (d/d elev, d/d az, d/ds_x, d/ds_y, d/ds_z)).
+    """
+    lib = _load()
+    h64 = _heights(h)
+    ny, nx = h64.shape
+    mode, n, uv, lift = _rays(uv, lift)
+    argmin = np.ascontiguousarray(argmin, dtype=np.int64)
+    gL = np.ascontiguousarray(gL, dtype=np.float64)
+    gh = np.zeros((ny, nx), np.float64)
+    gs = np.zeros(5, np.float64)
+    lib.or_grad(_ptr(h64), nx, ny, nx, float(g), float(radius), PROJ[proj], float(elev),
+                float(az), float(alpha), float(step_texels), mode, n, _ptr(uv), _ptr(lift),
+                _ptr(argmin), _ptr(gL), _ptr(gh), _ptr(gs))
+    return gh, gs
+
+
+def maxmip(h):
+    """Maximum mipmap: list of float32 levels [level0 (copy), level1, ...]."""
+    lib = _load()
+    h32 = np.ascontiguousarray(h, dtype=np.float32)
+    ny, nx = h32.shape
+    total, w, hh = 0, nx, ny
+    shapes = []
+    while w > 1 or hh > 1:
+        w, hh = (w + 1) // 2, (hh + 1) // 2
+        shapes.append((hh, w))
+        total += w * hh
+    out = np.empty(max(total, 1), np.float32)
+    L = lib.or_maxmip(_ptr(h32), nx, ny, nx, _ptr(out))
+    assert L == len(shapes) + 1
+    levels = [h32.copy()]
+    off = 0
+    for (hh, w) in shapes:
+        levels.append(out[off:off + w * hh].reshape(hh, w).copy())
+        off += w * hh
+    return levels
