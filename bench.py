@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Shadow rays/s of the exact max-mip descent on the 'mid' lunar workload.
+
+Workload (one step): 4096 x 4096 float32 heightfield (10 m/texel, seeded fBm +
+500 craters, +-1.5 km) on a sphere R = 1737.4 km, one shadow ray per texel
+centre (16,777,216 rays), sun elevation 1.0 deg, azimuth 120 deg, angular
+radius 0.2665 deg, max ray length 60 km (12,000 samples at 0.5 texel).
+A step = maximum-mipmap build + exact descent forward (light + argmin per ray).
+Inputs (64 MiB heights + 21 MiB pyramid) are smaller than L2, so L2 is flushed
+(a 512 MiB write) before every timed step.
+
+Printed JSON line: value = rays/s over all ranks (weak scaling: every rank runs
+its own full tile).  Extra keys: the same-GPU uniform-stepping kernel (same
+leaf values), forward+backward rays/s, the mipmap build alone, the roofline of
+the descent kernel, the FP64 oracle timed on host cores, and clocks.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project: there is no runnable reference implementation) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shadow rays/s (DP+maxmip vs uniform stepping, same GB300, <=1e-5 err); fwd+bwd rays/s"
+UNIT = "rays/s"
+CONFIG = "mid"
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-extras", action="store_true", help="skip uniform/backward/e2e/oracle legs")
+    p.add_argument("--leaf-level", type=int, default=-1)
+    p.add_argument("--block", type=int, default=0)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args(argv)
+
+
+# ----------------------------------------------------------------- ranks
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def reduce_max(value, dist_mod, device=None):
+    """Max of a float over all ranks (identity when not distributed)."""
+    if dist_mod is None or not dist_mod.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(rays_per_rank, n_ranks, steps, seconds_max):
+    """Whole-job throughput: every rank processes rays_per_rank per step."""
+    return rays_per_rank * n_ranks * steps / seconds_max
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_rate(inst, seconds, seed=2005):
+    """The FP64 oracle as it stands, on a seeded sample of the workload's rays,
+    sized to about `seconds` of work on all host cores.  Returns (rays/s, cores, sample)."""
+    import numpy as np
+    import oracle
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][0]
+    ny, nx = h.shape
+    rng = np.random.default_rng(seed)
+
+    def run(n):
+        ids = rng.choice(nx * ny, n, replace=False)
+        uv = np.stack([ids % nx, ids // nx], 1).astype(np.float32)
+        t0 = time.perf_counter()
+        oracle.shadow(h, g, inst["radius"], elev, az, inst["alpha"], inst["lmax"], uv=uv)
+        return time.perf_counter() - t0
+
+    n0 = 256
+    t0 = run(n0)
+    n = int(max(n0, min(4_000_000, n0 * seconds / max(t0, 1e-3))))
+    t = run(n)
+    cores = oracle.num_threads()
+    sample = (f"{n} seeded random rays of the {nx}x{ny} tile (every one of the "
+              f"{int(inst['lmax'] / (0.5 * g))} samples per ray evaluated in FP64)")
+    return n / t, cores, sample, n, t
+
+
+# -------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2005_06671_gb300 as ss
+    from workloads import make_instance
+
+    rank, local_rank, world = rank_info()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+
+    inst = make_instance(CONFIG)
+    h_np = inst["h"]
+    ny, nx = h_np.shape
+    n_rays = nx * ny
+    elev, az = inst["suns"][0]
+    lmax = inst["lmax"]
+    hf = ss.Heightfield(torch.from_numpy(h_np).to(dev), inst["g"], inst["radius"])
+    sun = ss.Sun(elev, az, inst["alpha"])
+    mip = torch.empty(ss.maxmip_bytes(nx, ny) // 4, dtype=torch.float32, device=dev)
+    light = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    argmin = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    bufs = dict(light=light, argmin=argmin)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    mip_launches = len(ss.maxmip_layout(nx, ny)) - 1
+    mip_passes = math.ceil(mip_launches / 6)
+
+    def step():
+        ss.ss_build_maxmip(hf, mip)
+        ss.ss_shadow_forward(hf, mip, sun, lmax, out=bufs, want_cost=False,
+                             leaf_level=args.leaf_level, block_threads=args.block)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, events on the launch stream
+    sampler = ClockSampler(local_rank)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        ss.ss_build_maxmip(hf, mip)
+        e1.record(stream)
+        ss.ss_shadow_forward(hf, mip, sun, lmax, out=bufs, want_cost=False,
+                             leaf_level=args.leaf_level, block_threads=args.block)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    mip_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    fwd_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    total_s = reduce_max(sum(step_ms) / 1e3, dist, dev)
+    value = weak_scaling_value(n_rays, world, args.steps, total_s)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded fBm + crater lunar terrain)",
+        "config": {"workload": f"mid: {nx}x{ny} f32 heightfield, 10 m/texel, one ray per texel "
+                               f"({n_rays} rays), sun elev 1.0 deg az 120 deg, Lmax 60 km, "
+                               f"0.5-texel samples; step = maxmip build + descent forward",
+                   "rays_per_step": n_rays, "l2": "flushed before every timed step (512 MiB write)",
+                   "parallelism": f"replicas x{world} (weak)"},
+        "clocks": clocks,
+        "gpu_launches": (mip_passes + 1) * args.steps,
+        "mip_build_ms": statistics.median(mip_ms),
+        "forward_ms": statistics.median(fwd_ms),
+    }
+    if rank != 0 or args.no_extras:
+        if rank == 0:
+            print(json.dumps(out))
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the descent kernel: gathered bytes from counted probes
+    res = ss.ss_shadow_forward(hf, mip, sun, lmax, count_samples=True, want_cost=False,
+                               leaf_level=args.leaf_level, block_threads=args.block)
+    cnt = res["counters"].to(torch.int64).sum(0).cpu().numpy()
+    bytes_fwd = 16.0 * (cnt[0] + cnt[1]) + 8.0 * n_rays
+    fwd_s = statistics.mean(fwd_ms) / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_fwd / fwd_s / 1e9
+    out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": "dp_forward_kernel",
+                       "algorithmic_bytes": bytes_fwd,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800",
+                       "mean_bound_probes_per_ray": float(cnt[0]) / n_rays,
+                       "mean_leaf_samples_per_ray": float(cnt[1]) / n_rays}
+    mip_bytes = 4.0 * n_rays + 4.0 * (ss.maxmip_bytes(nx, ny) / 4)
+    out["mip_roofline"] = {"achieved": mip_bytes / (statistics.median(mip_ms) / 1e3) / 1e9,
+                           "peak": peak, "unit": "GB/s"}
+
+    # ---- same-GPU uniform stepping (same leaf values), timed the same way
+    ures = ss.ss_shadow_uniform(hf, mip, sun, lmax, count_samples=True, want_cost=False)
+    ucnt = ures["counters"].to(torch.int64).sum(0).cpu().numpy()
+    u_ms = []
+    for k in range(3):
+        flush.zero_()
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        ss.ss_build_maxmip(hf, mip)
+        e1.record(stream)
+        ss.ss_shadow_uniform(hf, mip, sun, lmax, out=bufs, want_cost=False)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        u_ms.append(e0.elapsed_time(e2))
+    uni_value = n_rays / (statistics.mean(u_ms) / 1e3)
+    out["uniform"] = {"value": uni_value, "unit": UNIT, "ms_per_step": statistics.mean(u_ms),
+                      "mean_leaf_samples_per_ray": float(ucnt[1]) / n_rays,
+                      "same_results_as_descent": bool(torch.equal(ures["argmin"], res["argmin"]))}
+    out["speedup_vs_uniform"] = value / uni_value
+
+    # ---- forward + backward (loss gradient of ones), rays/s
+    gl = torch.ones(n_rays, dtype=torch.float32, device=dev)
+    gh = torch.zeros_like(hf.h)
+    gs = torch.zeros(5, dtype=torch.float64, device=dev)
+    fb_ms = []
+    for k in range(3):
+        flush.zero_()
+        gh.zero_()
+        gs.zero_()
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        ss.ss_build_maxmip(hf, mip)
+        ss.ss_shadow_forward(hf, mip, sun, lmax, out=bufs, want_cost=False)
+        e1.record(stream)
+        ss.ss_shadow_backward(hf, sun, lmax, argmin, gl, grad_h=gh, grad_sun=gs)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fb_ms.append(e0.elapsed_time(e2))
+    out["fwd_bwd"] = {"value": n_rays / (statistics.mean(fb_ms) / 1e3), "unit": UNIT,
+                      "ms_per_step": statistics.mean(fb_ms)}
+
+    # ---- end to end through the public API with host buffers
+    h_host = torch.from_numpy(h_np).pin_memory()
+    light_host = torch.empty(n_rays, dtype=torch.float32).pin_memory()
+    arg_host = torch.empty(n_rays, dtype=torch.int32).pin_memory()
+    hdev = torch.empty_like(hf.h)
+    hf2 = ss.Heightfield(hdev, inst["g"], inst["radius"])
+    e2e_ms = []
+    for k in range(max(3, min(args.steps, 5)) + 1):
+        flush.zero_()
+        e0, _, e2 = ev[0]
+        e0.record(stream)
+        hdev.copy_(h_host, non_blocking=True)
+        ss.ss_build_maxmip(hf2, mip)
+        ss.ss_shadow_forward(hf2, mip, sun, lmax, out=bufs, want_cost=False)
+        light_host.copy_(light, non_blocking=True)
+        arg_host.copy_(argmin, non_blocking=True)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_ms.append(e0.elapsed_time(e2))
+    out["e2e"] = {"value": n_rays / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
+                  "h2d_bytes_per_step": int(h_host.numel() * 4),
+                  "d2h_bytes_per_step": int(light_host.numel() * 4 + arg_host.numel() * 4),
+                  "ms_per_step": statistics.mean(e2e_ms)}
+
+    # ---- CPU oracle on the machine's host cores (bounded sample)
+    rate, cores, sample, n, t = oracle_rate(inst, args.cpu_seconds)
+    out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": sample, "seconds": t}
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, _, world = rank_info()
+    if rank != 0:
+        return
+    from workloads import make_instance
+    import numpy as np
+    import oracle
+    inst = make_instance(CONFIG)
+    ny, nx = inst["h"].shape
+    # each step: a fixed seeded sample of the workload's rays, about 3 s of CPU work
+    _, cores, _, n, t = oracle_rate(inst, 3.0, seed=1)
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][0]
+    rng = np.random.default_rng(7)
+    ids = rng.choice(nx * ny, n, replace=False)
+    uv = np.stack([ids % nx, ids // nx], 1).astype(np.float32)
+
+    def step():
+        oracle.shadow(h, g, inst["radius"], elev, az, inst["alpha"], inst["lmax"], uv=uv)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    sample = f"{n} seeded random rays of the {nx}x{ny} 'mid' tile per step (FP64, every sample)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded fBm + crater lunar terrain)",
+        "config": {"workload": f"mid: {nx}x{ny} f32 heightfield, 10 m/texel, sun elev 1.0 deg "
+                               f"az 120 deg, Lmax 60 km; bounded ray sample per step",
+                   "rays_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

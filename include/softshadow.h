@@ -1,0 +1,190 @@
+/*
+ * softshadow.h -- C ABI of the GB300 soft-shadow library (libsoftshadow.so).
+ *
+ * Soft shadows on a heightfield draped on a sphere, after Jung, Schrempp & Son,
+ * "Optimally Fast Soft Shadows on Curved Terrain with Dynamic Programming and
+ * Maximum Mipmaps" (arXiv 2005.06671).  For each surface point p one shadow ray
+ * p + t*L is cast toward the centre of the sun (Sec. 3.1); its cost is the
+ * clearance between the ray and the terrain divided by the distance travelled,
+ * minimised over the ray (Eq. shadowfrac, final step of Algorithm 1); the
+ * light fraction is the part of the sun disc left above the horizon chord that
+ * cost implies (Eqs. discsegment/discfrac, Sec. 3.4).  The minimum is found by a
+ * descent over a maximum mipmap (Sec. 3.2, "Dynamic Programming", "Maximum
+ * mipmaps") made exact: every sample whose cost could beat the running minimum
+ * is evaluated, so the result equals evaluating every sample.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Geometry.  Sphere of radius R centred at the origin.  Tile frame: x = grid +u
+ * (columns), y = grid +v (rows), z = direction of the tile centre.  Texel (u, v)
+ * (0-based column, row) sits at plane coordinates X = (u - (nx-1)/2)*g,
+ * Y = (v - (ny-1)/2)*g, mapped to the sphere gnomonically (direction
+ * (X, Y, R)/|.|; a straight 3-D ray maps to a straight texture line, Sec. 3.2,
+ * Appendix "Deriving T") or by polar stereographic projection (tile centred on
+ * the pole).  Heights h are metres above the sphere.  Bilinear interpolation
+ * uses base texel min(floor(u), nx-2); the usable domain is [0,nx-1]x[0,ny-1].
+ * Sun direction s = (cos e sin a, cos e cos a, sin e) in the tile frame:
+ * elevation e, azimuth a measured from grid +y toward grid +x.
+ * Samples t_j = j * delta (j = 1 .. floor(max_len/delta)), delta = step_texels*g;
+ * a sample is used when its texel image lies in the usable domain.
+ *   cost c_j   = (|p + t_j s| - R - h(sample)) / t_j          [rad]
+ *   c*         = min_j c_j, argmin j* = smallest j attaining it (1-based),
+ *                or c* = +inf, j* = -1 when no sample is usable
+ *   d          = clamp(c* cos(eps_p) / alpha, -1, 1), sin(eps_p) = n_p . s
+ *   light      = (pi - acos d + d sqrt(1 - d^2)) / pi          (1 when j* = -1)
+ *
+ * Memory.  Every pointer named "device" is CUDA device memory owned by the
+ * caller; the library never allocates device memory.  Heights are float32,
+ * row-major, row stride pitch (elements).  Inputs must be finite.
+ *
+ * Streams.  Every call that takes an ss_stream_t enqueues its work on that
+ * stream (NULL = the legacy default stream) and returns without synchronising.
+ *
+ * Errors.  Argument errors are detected on the host before anything is
+ * enqueued and returned synchronously; CUDA launch errors map to SS_ERR_CUDA
+ * (details: ss_last_error_string()).  Nothing is launched when a call fails
+ * validation.
+ */
+#ifndef SOFTSHADOW_H
+#define SOFTSHADOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ss_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    SS_OK = 0,
+    SS_ERR_INVALID_ARG = 1,   /* null pointer, non-finite or out-of-range scalar */
+    SS_ERR_BAD_SIZE = 2,      /* nx/ny/pitch/ray count out of range            */
+    SS_ERR_OUT_OF_MEMORY = 3, /* caller-supplied workspace too small            */
+    SS_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed           */
+    SS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up             */
+    SS_ERR_INTERNAL = 6,      /* device-side consistency check failed           */
+    SS_ERR_UNSUPPORTED = 7    /* valid request this build does not implement     */
+} ss_status;
+
+enum { SS_PROJ_GNOMONIC = 0, SS_PROJ_POLAR_STEREO = 1 };
+enum { SS_RAYS_GRID = 0, SS_RAYS_LIST = 1 };
+
+/* ss_params.flags */
+#define SS_FLAG_COUNT_SAMPLES 0x1u /* fill ss_outputs.counters                      */
+#define SS_FLAG_NO_EARLY_EXIT 0x2u /* ss_shadow_uniform: evaluate every usable sample */
+
+/* Largest supported tile edge and ray length (samples): sample indices and
+ * texel coordinates are exact in float32 below these bounds. */
+#define SS_MAX_DIM 65536
+#define SS_MAX_SAMPLES 65535
+
+/* Heightfield tile (Sec. 3.2: texture of heights draped on the sphere). */
+typedef struct {
+    const float* h;        /* device, [ny][pitch] float32 heights (m)          */
+    int32_t nx, ny;        /* columns, rows; each in [2, SS_MAX_DIM]           */
+    int64_t pitch;         /* row stride in elements, >= nx                    */
+    double texel_m;        /* g: texel size on the projection plane (m), > 0   */
+    double radius_m;       /* R: sphere radius (m), > 0                        */
+    int32_t projection;    /* SS_PROJ_*                                        */
+} ss_heightfield;
+
+/* Light source: direction and angular radius r_L (Sec. 3.4). */
+typedef struct {
+    double elevation_rad;       /* e, in (-pi/2, pi/2)                         */
+    double azimuth_rad;         /* a, from grid +y toward grid +x              */
+    double angular_radius_rad;  /* alpha = r_L > 0                             */
+} ss_sun;
+
+typedef struct {
+    double max_len_m;      /* Lmax: longest ray (m), > 0                       */
+    double step_texels;    /* delta / g; 0 selects 0.5                         */
+    uint32_t flags;        /* SS_FLAG_*                                        */
+    int32_t block_threads; /* threads per block; 0 = default                   */
+    int32_t leaf_level;    /* forward: subtrees of <= 2^leaf_level samples are
+                              evaluated sample by sample; -1 = default         */
+    int32_t reserved;      /* must be 0                                        */
+} ss_params;
+
+/* Ray origins p (Sec. 3.1: view-ray intersection points). */
+typedef struct {
+    int32_t mode;          /* SS_RAYS_GRID: one ray per texel centre, ray r at
+                              (r % nx, r / nx), n = nx*ny;
+                              SS_RAYS_LIST: n rays at uv[2r], uv[2r+1]        */
+    int64_t n;             /* list mode: number of rays, >= 0                  */
+    const float* uv;       /* device, [n][2] texel coordinates (list mode)     */
+    const float* lift_m;   /* device, [n] metres above the surface, or NULL    */
+} ss_rays;
+
+/* Per-ray outputs, all device arrays of n entries. */
+typedef struct {
+    float* light;          /* required: lit fraction in [0, 1]                 */
+    int32_t* argmin;       /* required: j* (1-based) or -1                     */
+    float* cost;           /* optional: c* in rad (+inf when j* = -1), or NULL */
+    int32_t* counters;     /* optional [n][2]: (bound probes, leaf samples)
+                              when SS_FLAG_COUNT_SAMPLES is set, or NULL       */
+} ss_outputs;
+
+/* ---------------------------------------------------------------- general */
+const char* ss_status_string(ss_status status);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char* ss_last_error_string(void);
+const char* ss_version(void);
+
+/* ------------------------------------------------------- maximum mipmap
+ * Sec. 3.2 "Maximum mipmaps": level 0 is the heightfield; level l+1 has
+ * ceil(w/2) x ceil(h/2) texels, each the maximum of the (up to) 2x2 texels of
+ * level l below it; levels continue down to 1x1.  The library stores levels
+ * 1..L-1 in one caller-allocated device buffer: level l starts at element
+ * offset_elems (256-byte aligned) and has row stride pitch (a multiple of 4
+ * elements).  Two float32 scalars follow the levels: [stats] = (global max,
+ * global min) of the heightfield. */
+int32_t ss_maxmip_levels(int32_t nx, int32_t ny);          /* L, or 0 on bad size */
+size_t ss_maxmip_bytes(int32_t nx, int32_t ny);            /* 0 on bad size       */
+ss_status ss_maxmip_level_info(int32_t nx, int32_t ny, int32_t level, int32_t* width,
+                               int32_t* height, int64_t* pitch, int64_t* offset_elems);
+/* Builds every level of hf->h's pyramid into mip (device, ss_maxmip_bytes).
+ * Bit-exact: each texel is exactly one of the input values. */
+ss_status ss_build_maxmip(const ss_heightfield* hf, float* mip, ss_stream_t stream);
+
+/* ----------------------------------------------------------- forward
+ * Exact descent over the maximum mipmap (Sec. 3.2 "Dynamic Programming",
+ * Eq. optimumk2: the clearance over an interval is bounded through the maximum
+ * height below it).  Aligned blocks of samples are bounded by the mip maximum
+ * over their texel footprint; blocks whose bound cannot beat the running
+ * minimum are skipped; the rest are split until single samples are evaluated.
+ * Sample values are float32 in a per-ray local frame (FP64 per-ray setup); the
+ * argmin sample of rays with unsaturated light is re-evaluated in FP64.
+ * mip: device, built by ss_build_maxmip for the same heights. */
+ss_status ss_shadow_forward(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                            const ss_sun* sun, const ss_params* params,
+                            const ss_outputs* out, ss_stream_t stream);
+
+/* Uniform ray stepping (Sec. 2, Fig. 1b): every usable sample in order, with an
+ * exact early exit once (H(t) - max h)/t, non-decreasing in t, reaches the
+ * running minimum.  Same sample values as ss_shadow_forward, so both return the
+ * same argmin and cost bit for bit.  mip: used only for the global max. */
+ss_status ss_shadow_uniform(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                            const ss_sun* sun, const ss_params* params,
+                            const ss_outputs* out, ss_stream_t stream);
+
+/* ---------------------------------------------------------- backward
+ * Adjoint of light with respect to the heights and the sun direction, at each
+ * ray's forward argmin (a subgradient of the minimum; derived from Eq. discfrac
+ * and the sample cost).  Inputs: argmin from ss_shadow_forward, grad_light (device
+ * [n] float32, dLoss/dlight).  grad_h (device, [ny][pitch] float32) is
+ * ACCUMULATED into (zero it first); grad_sun (device double[5]) is accumulated:
+ * (dL/d elevation, dL/d azimuth, dL/ds_x, dL/ds_y, dL/ds_z), s a free 3-vector.
+ * Rays with j* = -1 or saturated light contribute nothing.  Atomic
+ * accumulation: summation order, and so the last bits, may vary between runs. */
+ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, const ss_sun* sun,
+                             const ss_params* params, const int32_t* argmin,
+                             const float* grad_light, float* grad_h, double* grad_sun,
+                             ss_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOFTSHADOW_H */

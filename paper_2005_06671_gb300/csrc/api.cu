@@ -1,0 +1,277 @@
+// C ABI (include/softshadow.h): argument validation on the host, then kernel
+// launches on the caller's stream.  Nothing here allocates device memory.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/softshadow.h"
+#include "ss_launch.h"
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+ss_status cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    return SS_ERR_CUDA;
+}
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+ss_status check_tile(const ss_heightfield* hf, int32_t min_dim) {
+    if (!hf || !hf->h) return SS_ERR_INVALID_ARG;
+    if (hf->nx < min_dim || hf->ny < min_dim || hf->nx > SS_MAX_DIM || hf->ny > SS_MAX_DIM)
+        return SS_ERR_BAD_SIZE;
+    if (hf->pitch < hf->nx) return SS_ERR_BAD_SIZE;
+    if (!finite_pos(hf->texel_m) || !finite_pos(hf->radius_m)) return SS_ERR_INVALID_ARG;
+    if (hf->projection != SS_PROJ_GNOMONIC && hf->projection != SS_PROJ_POLAR_STEREO)
+        return SS_ERR_INVALID_ARG;
+    return SS_OK;
+}
+
+ss_status check_sun(const ss_sun* sun) {
+    if (!sun) return SS_ERR_INVALID_ARG;
+    if (!isfinite(sun->elevation_rad) || !isfinite(sun->azimuth_rad)) return SS_ERR_INVALID_ARG;
+    if (!(fabs(sun->elevation_rad) < M_PI / 2)) return SS_ERR_INVALID_ARG;
+    if (!finite_pos(sun->angular_radius_rad) || !(sun->angular_radius_rad < M_PI / 2))
+        return SS_ERR_INVALID_ARG;
+    return SS_OK;
+}
+
+ss_status check_params(const ss_params* p, double g, int32_t* J, double* delta) {
+    if (!p) return SS_ERR_INVALID_ARG;
+    if (!finite_pos(p->max_len_m)) return SS_ERR_INVALID_ARG;
+    if (!isfinite(p->step_texels) || p->step_texels < 0.0) return SS_ERR_INVALID_ARG;
+    if (p->flags & ~(SS_FLAG_COUNT_SAMPLES | SS_FLAG_NO_EARLY_EXIT)) return SS_ERR_INVALID_ARG;
+    if (p->block_threads != 0 &&
+        (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32 != 0))
+        return SS_ERR_INVALID_ARG;
+    if (p->leaf_level < -1 || p->leaf_level > 16) return SS_ERR_INVALID_ARG;
+    if (p->reserved != 0) return SS_ERR_INVALID_ARG;
+    double st = p->step_texels == 0.0 ? 0.5 : p->step_texels;
+    double d = st * g;
+    if (!finite_pos(d)) return SS_ERR_INVALID_ARG;
+    double jj = floor(p->max_len_m / d);
+    if (!(jj <= (double)SS_MAX_SAMPLES)) return SS_ERR_BAD_SIZE;
+    *J = (int32_t)jj;
+    *delta = d;
+    return SS_OK;
+}
+
+ss_status check_rays(const ss_rays* r, const ss_heightfield* hf, int64_t* n) {
+    if (!r) return SS_ERR_INVALID_ARG;
+    if (r->mode == SS_RAYS_GRID) {
+        *n = (int64_t)hf->nx * hf->ny;
+    } else if (r->mode == SS_RAYS_LIST) {
+        if (r->n < 0) return SS_ERR_BAD_SIZE;
+        if (r->n > 0 && !r->uv) return SS_ERR_INVALID_ARG;
+        *n = r->n;
+    } else {
+        return SS_ERR_INVALID_ARG;
+    }
+    return SS_OK;
+}
+
+void sun_vector(const ss_sun* s, double v[3]) {
+    double ce = cos(s->elevation_rad);
+    v[0] = ce * sin(s->azimuth_rad);
+    v[1] = ce * cos(s->azimuth_rad);
+    v[2] = sin(s->elevation_rad);
+}
+
+ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, double delta) {
+    ss::Tile T{};
+    T.h = hf->h;
+    T.pitch = hf->pitch;
+    T.nx = hf->nx;
+    T.ny = hf->ny;
+    T.proj = hf->projection;
+    T.J = J;
+    T.g = hf->texel_m;
+    T.R = hf->radius_m;
+    T.cx = 0.5 * (hf->nx - 1);
+    T.cy = 0.5 * (hf->ny - 1);
+    double s[3];
+    sun_vector(sun, s);
+    T.sx = s[0];
+    T.sy = s[1];
+    T.sz = s[2];
+    T.delta = delta;
+    T.inv_gR = 1.0 / (hf->texel_m * hf->radius_m);
+    T.alpha = sun->angular_radius_rad;
+    T.delta_f = (float)delta;
+    T.alpha_f = (float)sun->angular_radius_rad;
+    return T;
+}
+
+ss::Pyramid make_pyramid(const ss_heightfield* hf, const float* mip, const ss::MipLayout& L) {
+    ss::Pyramid P{};
+    P.levels = L.levels;
+    P.ptr[0] = hf->h;
+    P.pitch[0] = hf->pitch;
+    for (int l = 1; l < L.levels; ++l) {
+        P.ptr[l] = mip + L.offset[l];
+        P.pitch[l] = L.pitch[l];
+    }
+    return P;
+}
+
+enum class FwdKind { Descent, Uniform };
+
+ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip,
+                        const ss_rays* rays, const ss_sun* sun, const ss_params* params,
+                        const ss_outputs* out, ss_stream_t stream) {
+    ss_status st = check_tile(hf, 2);
+    if (st != SS_OK) return st;
+    if (hf->projection != SS_PROJ_GNOMONIC) return SS_ERR_UNSUPPORTED;
+    if ((st = check_sun(sun)) != SS_OK) return st;
+    int32_t J;
+    double delta;
+    if ((st = check_params(params, hf->texel_m, &J, &delta)) != SS_OK) return st;
+    int64_t n;
+    if ((st = check_rays(rays, hf, &n)) != SS_OK) return st;
+    if (!mip || !out) return SS_ERR_INVALID_ARG;
+    if (n == 0) return SS_OK;
+    if (!out->light || !out->argmin) return SS_ERR_INVALID_ARG;
+    if ((params->flags & SS_FLAG_COUNT_SAMPLES) && !out->counters) return SS_ERR_INVALID_ARG;
+    ss::MipLayout L;
+    if (!ss::mip_layout(hf->nx, hf->ny, &L)) return SS_ERR_BAD_SIZE;
+    ss::FwdArgs a{};
+    a.T = make_tile(hf, sun, J, delta);
+    a.P = make_pyramid(hf, mip, L);
+    a.R.mode = rays->mode;
+    a.R.n = n;
+    a.R.uv = rays->uv;
+    a.R.lift = rays->mode == SS_RAYS_LIST ? rays->lift_m : nullptr;
+    a.O.light = out->light;
+    a.O.argmin = out->argmin;
+    a.O.cost = out->cost;
+    a.O.counters = (params->flags & SS_FLAG_COUNT_SAMPLES) ? out->counters : nullptr;
+    a.stats = mip + L.stats_offset;
+    a.kleaf = params->leaf_level < 0 ? 3 : params->leaf_level;
+    a.flags = params->flags;
+    int block = params->block_threads ? params->block_threads : 256;
+    cudaError_t e = kind == FwdKind::Descent
+                        ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
+                        : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, kind == FwdKind::Descent ? "ss_shadow_forward" : "ss_shadow_uniform");
+    return SS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ss_status_string(ss_status s) {
+    switch (s) {
+        case SS_OK: return "SS_OK";
+        case SS_ERR_INVALID_ARG: return "SS_ERR_INVALID_ARG: invalid argument";
+        case SS_ERR_BAD_SIZE: return "SS_ERR_BAD_SIZE: size out of range";
+        case SS_ERR_OUT_OF_MEMORY: return "SS_ERR_OUT_OF_MEMORY: workspace too small";
+        case SS_ERR_CUDA: return "SS_ERR_CUDA: CUDA error";
+        case SS_ERR_TIMEOUT: return "SS_ERR_TIMEOUT: bounded device wait expired";
+        case SS_ERR_INTERNAL: return "SS_ERR_INTERNAL: internal consistency check failed";
+        case SS_ERR_UNSUPPORTED: return "SS_ERR_UNSUPPORTED: not supported by this build";
+    }
+    return "unknown ss_status";
+}
+
+const char* ss_last_error_string(void) { return g_last_error; }
+
+const char* ss_version(void) { return "softshadow-gb300 0.1 (sm_103a)"; }
+
+int32_t ss_maxmip_levels(int32_t nx, int32_t ny) {
+    ss::MipLayout L;
+    return ss::mip_layout(nx, ny, &L) ? L.levels : 0;
+}
+
+size_t ss_maxmip_bytes(int32_t nx, int32_t ny) {
+    ss::MipLayout L;
+    return ss::mip_layout(nx, ny, &L) ? (size_t)L.total_elems * sizeof(float) : 0;
+}
+
+ss_status ss_maxmip_level_info(int32_t nx, int32_t ny, int32_t level, int32_t* width,
+                               int32_t* height, int64_t* pitch, int64_t* offset_elems) {
+    ss::MipLayout L;
+    if (!ss::mip_layout(nx, ny, &L)) return SS_ERR_BAD_SIZE;
+    if (level < 0 || level > L.levels) return SS_ERR_INVALID_ARG;
+    if (level == L.levels) {   // the stats block
+        if (width) *width = 2;
+        if (height) *height = 1;
+        if (pitch) *pitch = 2;
+        if (offset_elems) *offset_elems = L.stats_offset;
+        return SS_OK;
+    }
+    if (width) *width = L.w[level];
+    if (height) *height = L.h[level];
+    if (pitch) *pitch = level == 0 ? (int64_t)nx : L.pitch[level];
+    if (offset_elems) *offset_elems = level == 0 ? -1 : L.offset[level];
+    return SS_OK;
+}
+
+ss_status ss_build_maxmip(const ss_heightfield* hf, float* mip, ss_stream_t stream) {
+    ss_status st = check_tile(hf, 1);
+    if (st != SS_OK) return st;
+    if (!mip) return SS_ERR_INVALID_ARG;
+    ss::MipLayout L;
+    if (!ss::mip_layout(hf->nx, hf->ny, &L)) return SS_ERR_BAD_SIZE;
+    cudaError_t e = ss::launch_build_maxmip(hf->h, hf->nx, hf->ny, hf->pitch, mip, L,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_build_maxmip");
+    return SS_OK;
+}
+
+ss_status ss_shadow_forward(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                            const ss_sun* sun, const ss_params* params, const ss_outputs* out,
+                            ss_stream_t stream) {
+    return shadow_common(FwdKind::Descent, hf, mip, rays, sun, params, out, stream);
+}
+
+ss_status ss_shadow_uniform(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                            const ss_sun* sun, const ss_params* params, const ss_outputs* out,
+                            ss_stream_t stream) {
+    return shadow_common(FwdKind::Uniform, hf, mip, rays, sun, params, out, stream);
+}
+
+ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, const ss_sun* sun,
+                             const ss_params* params, const int32_t* argmin,
+                             const float* grad_light, float* grad_h, double* grad_sun,
+                             ss_stream_t stream) {
+    ss_status st = check_tile(hf, 2);
+    if (st != SS_OK) return st;
+    if (hf->projection != SS_PROJ_GNOMONIC) return SS_ERR_UNSUPPORTED;
+    if ((st = check_sun(sun)) != SS_OK) return st;
+    int32_t J;
+    double delta;
+    if ((st = check_params(params, hf->texel_m, &J, &delta)) != SS_OK) return st;
+    int64_t n;
+    if ((st = check_rays(rays, hf, &n)) != SS_OK) return st;
+    if (n == 0) return SS_OK;
+    if (!argmin || !grad_light || !grad_h || !grad_sun) return SS_ERR_INVALID_ARG;
+    ss::BwdArgs a{};
+    a.T = make_tile(hf, sun, J, delta);
+    a.R.mode = rays->mode;
+    a.R.n = n;
+    a.R.uv = rays->uv;
+    a.R.lift = rays->mode == SS_RAYS_LIST ? rays->lift_m : nullptr;
+    a.argmin = argmin;
+    a.grad_light = grad_light;
+    a.grad_h = grad_h;
+    a.grad_pitch = hf->pitch;
+    a.grad_sun = grad_sun;
+    double e = sun->elevation_rad, az = sun->azimuth_rad;
+    a.ds_de[0] = -sin(e) * sin(az);
+    a.ds_de[1] = -sin(e) * cos(az);
+    a.ds_de[2] = cos(e);
+    a.ds_da[0] = cos(e) * cos(az);
+    a.ds_da[1] = -cos(e) * sin(az);
+    a.ds_da[2] = 0.0;
+    int block = params->block_threads ? params->block_threads : 256;
+    cudaError_t ce = ss::launch_backward(a, block, (cudaStream_t)stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ss_shadow_backward");
+    return SS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// Forward (exact max-mip descent and uniform stepping) and backward kernels.
+//
+// Work decomposition: one thread per shadow ray, rays taken in chunks of 32
+// consecutive ray ids per warp (grid mode: 32 neighbouring texels of a row,
+// whose samples at equal j touch neighbouring texels, so gathers coalesce),
+// chunks distributed grid-stride over a grid sized to the SM count.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ss_launch.h"
+
+namespace ss {
+
+__device__ __forceinline__ int64_t ray_count(const Tile& T, const Rays& R) {
+    return R.mode == 0 ? (int64_t)T.nx * T.ny : R.n;
+}
+
+// Final value of one ray: re-evaluate the argmin sample in FP64 when the light
+// is not saturated, then apply the disc-occlusion formula (Eq. discfrac).
+__device__ __forceinline__ void finish_ray(const FwdArgs& a, int64_t r, const RayF& rf,
+                                           float best, int32_t bestj, int32_t nb, int32_t nl) {
+    float light, cost;
+    if (bestj < 0) {
+        light = 1.0f;
+        cost = INFINITY;
+    } else {
+        float d = best * rf.cos_e / a.T.alpha_f;
+        if (fabsf(d) < 1.001f) {
+            double up, vp, hp, href, ow[4];
+            int32_t oi0, oj0;
+            ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
+            Geom64 G;
+            geom64(a.T, up, vp, hp, G);
+            double c = leaf_cost64(a.T, G, bestj);
+            double dd = c * G.cos_e / a.T.alpha;
+            light = (float)disc_light64(dd);
+            cost = (float)c;
+        } else {
+            light = d > 0.0f ? 1.0f : 0.0f;
+            cost = best;
+        }
+    }
+    a.O.light[r] = light;
+    a.O.argmin[r] = bestj;
+    if (a.O.cost) a.O.cost[r] = cost;
+    if (a.O.counters) {
+        a.O.counters[2 * r] = nb;
+        a.O.counters[2 * r + 1] = nl;
+    }
+}
+
+__device__ __forceinline__ void setup_ray(const FwdArgs& a, int64_t r, float span, RayF& rf) {
+    double up, vp, hp, href, ow[4];
+    int32_t oi0, oj0;
+    ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
+    Geom64 G;
+    geom64(a.T, up, vp, hp, G);
+    make_rayf(a.T, G, href, span, rf);
+}
+
+// ---------------------------------------------------------------- descent
+// Stackless depth-first walk over aligned sample blocks [s0+1, s0+2^k]:
+// a block is bounded through the mip (node_bound) and skipped when its bound
+// exceeds the running minimum, else split; blocks of <= 2^kleaf samples are
+// evaluated sample by sample.  After a block, the walk continues at
+// s0 += 2^k with k = ctz(s0) -- the next block in near-to-far order.  Samples
+// are therefore evaluated in increasing j, and a strict '<' keeps the smallest
+// j among equal costs.
+template <bool kCount>
+__global__ void __launch_bounds__(256) dp_forward_kernel(const FwdArgs a) {
+    __shared__ const float* s_ptr[kMaxLevels];
+    __shared__ int64_t s_pitch[kMaxLevels];
+    if (threadIdx.x < kMaxLevels) {
+        s_ptr[threadIdx.x] = a.P.ptr[threadIdx.x];
+        s_pitch[threadIdx.x] = a.P.pitch[threadIdx.x];
+    }
+    __syncthreads();
+    const float span = a.stats[0] - a.stats[1];
+    const int64_t n = ray_count(a.T, a.R);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int32_t kleaf = a.kleaf;
+
+    for (int64_t base = warp * 32; base < n; base += warps * 32) {
+        const int64_t r = base + lane;
+        if (r >= n) continue;
+        RayF rf;
+        setup_ray(a, r, span, rf);
+        float best = INFINITY;
+        int32_t bestj = -1, nb = 0, nl = 0;
+        const int32_t jlo = rf.j_lo, jhi = rf.j_hi;
+        if (jhi >= jlo) {
+            int32_t K = jhi <= 1 ? 0 : 32 - __clz(jhi - 1);   // 2^K >= jhi
+            int32_t s0 = 0;
+            int32_t k = K > kleaf ? K : 0;
+            while (true) {
+                bool advance = true;
+                if (k > 0) {
+                    int32_t ja = max(s0 + 1, jlo), jb = min(s0 + (1 << k), jhi);
+                    if (ja <= jb) {
+                        float lb = node_bound(a.T, a.P, s_ptr, s_pitch, rf, ja, jb);
+                        if (kCount) ++nb;
+                        if (!(lb > best)) {
+                            k = (k - 1 > kleaf) ? k - 1 : 0;
+                            advance = false;
+                        }
+                    }
+                } else {
+                    int32_t j = s0 + 1;
+                    if (j >= jlo) {
+                        float c = leaf_cost(a.T, rf, j);
+                        if (kCount) ++nl;
+                        if (c < best) {
+                            best = c;
+                            bestj = j;
+                        }
+                    }
+                }
+                if (advance) {
+                    s0 += 1 << k;
+                    if (s0 >= jhi) break;
+                    k = __ffs(s0) - 1;
+                    if (k <= kleaf) k = 0;
+                }
+            }
+        }
+        finish_ray(a, r, rf, best, bestj, nb, nl);
+    }
+}
+
+// ---------------------------------------------------------------- uniform
+// Every usable sample in order.  Early exit (exact): with H(t) = h_p + rise(t)
+// convex and H(0) = h_p <= max h, g(t) = (H(t) - max h - G)/t is
+// non-decreasing and bounds every later sample's cost from below; once
+// g(t_j) >= best no later sample can win.  G = 3 guards covers the float32
+// rounding of both sides.
+template <bool kCount>
+__global__ void __launch_bounds__(256) uniform_forward_kernel(const FwdArgs a) {
+    const float hmax = a.stats[0];
+    const float span = a.stats[0] - a.stats[1];
+    const int64_t n = ray_count(a.T, a.R);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const bool allow_exit = !(a.flags & 0x2u);
+
+    for (int64_t base = warp * 32; base < n; base += warps * 32) {
+        const int64_t r = base + lane;
+        if (r >= n) continue;
+        RayF rf;
+        setup_ray(a, r, span, rf);
+        float best = INFINITY;
+        int32_t bestj = -1, nl = 0;
+        const float hmax_rel = hmax - rf.href;
+        const bool exit_ok = allow_exit && (rf.X <= hmax_rel);
+        const float tJ = (float)rf.j_hi * a.T.delta_f;
+        const float rb = fmaxf(rise_bound(rf, tJ), 0.25f * rf.B * rf.B * rf.inv_rho);
+        const float G = 3.0f * kGuardRel * (rf.guard0 + fabsf(hmax_rel) + rb);
+        for (int32_t j = rf.j_lo; j <= rf.j_hi; ++j) {
+            float rise;
+            float c = leaf_cost(a.T, rf, j, &rise);
+            if (kCount) ++nl;
+            if (c < best) {
+                best = c;
+                bestj = j;
+            }
+            if (exit_ok && (j & 3) == 0) {
+                float t = (float)j * a.T.delta_f;
+                float g = (((rf.X + rise) - hmax_rel) - G) / t;
+                if (g >= best) break;
+            }
+        }
+        finish_ray(a, r, rf, best, bestj, 0, nl);
+    }
+}
+
+// ---------------------------------------------------------------- backward
+// d light / d (heights, sun) at the forward argmin, FP64 per ray (only rays in
+// the penumbra have a non-zero gradient).  Heights: atomicAdd (float32);
+// sun: block reduction in FP64, then one atomicAdd per block and component.
+__global__ void __launch_bounds__(256) backward_kernel(const BwdArgs a) {
+    const int64_t n = ray_count(a.T, a.R);
+    double gs[5] = { 0.0, 0.0, 0.0, 0.0, 0.0 };
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        int32_t j = a.argmin[r];
+        float gl = a.grad_light[r];
+        if (j < 1 || gl == 0.0f) continue;
+        double up, vp, hp, href, ow[4];
+        int32_t oi0, oj0;
+        ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
+        Geom64 G;
+        geom64(a.T, up, vp, hp, G);
+        double U, V;
+        double c = leaf_cost64(a.T, G, j, &U, &V);
+        double d = c * G.cos_e / a.T.alpha;
+        if (!(d > -1.0 && d < 1.0)) continue;
+        double gd = (double)gl * (2.0 / M_PI) * sqrt(1.0 - d * d);   // dL/dd
+        double gc = gd * G.cos_e / a.T.alpha;                         // dL/dc
+        double t = (double)j * a.T.delta;
+        // sample texels and the bilinear gradient at (U, V)
+        int32_t i0 = (int32_t)floor(U), j0 = (int32_t)floor(V);
+        i0 = min(max(i0, 0), a.T.nx - 2);
+        j0 = min(max(j0, 0), a.T.ny - 2);
+        double fu = U - i0, fv = V - j0;
+        const float* hr = a.T.h + (int64_t)j0 * a.T.pitch + i0;
+        double h00 = hr[0], h10 = hr[1], h01 = hr[a.T.pitch], h11 = hr[a.T.pitch + 1];
+        double du = (1.0 - fv) * (h10 - h00) + fv * (h11 - h01);
+        double dv = (1.0 - fu) * (h01 - h00) + fu * (h11 - h10);
+        double w[4] = { (1.0 - fu) * (1.0 - fv), fu * (1.0 - fv), (1.0 - fu) * fv, fu * fv };
+        float* gp = a.grad_h + (int64_t)j0 * a.grad_pitch + i0;
+        atomicAdd(gp, (float)(-gc * w[0] / t));
+        atomicAdd(gp + 1, (float)(-gc * w[1] / t));
+        atomicAdd(gp + a.grad_pitch, (float)(-gc * w[2] / t));
+        atomicAdd(gp + a.grad_pitch + 1, (float)(-gc * w[3] / t));
+        // origin height: moves the ray up along n_p and shifts its texel image
+        double B = 2.0 * G.rho * G.sin_e;
+        double qn = sqrt(G.rho * G.rho + t * (B + t));
+        double dHdhp = (G.rho + t * G.sin_e) / qn;
+        double jd = (double)j, den = 1.0 + G.b * jd;
+        double dUdhp = -G.Au * jd / (G.rho * den * den);
+        double dVdhp = -G.Av * jd / (G.rho * den * den);
+        double dcdhp = (dHdhp - (du * dUdhp + dv * dVdhp)) / t;
+        float* go = a.grad_h + (int64_t)oj0 * a.grad_pitch + oi0;
+        double go_s = gc * dcdhp;
+        if (ow[0] != 0.0) atomicAdd(go, (float)(go_s * ow[0]));
+        if (ow[1] != 0.0) atomicAdd(go + 1, (float)(go_s * ow[1]));
+        if (ow[2] != 0.0) atomicAdd(go + a.grad_pitch, (float)(go_s * ow[2]));
+        if (ow[3] != 0.0) atomicAdd(go + a.grad_pitch + 1, (float)(go_s * ow[3]));
+        // sun direction: q = p + t s; dc/ds = q/|q| - grad_q h(texel image of q)
+        double q[3] = { G.rho * G.nhat[0] + t * a.T.sx, G.rho * G.nhat[1] + t * a.T.sy,
+                        G.rho * G.nhat[2] + t * a.T.sz };
+        double kq = a.T.R / a.T.g;
+        double JU[3] = { kq / q[2], 0.0, -kq * q[0] / (q[2] * q[2]) };
+        double JV[3] = { 0.0, kq / q[2], -kq * q[1] / (q[2] * q[2]) };
+        double ce_term = G.cos_e > 0.0 ? (-G.sin_e / G.cos_e) : 0.0;
+        double gsv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            double dcds = q[i] / qn - (du * JU[i] + dv * JV[i]);
+            gsv[i] = gc * dcds + gd * (c / a.T.alpha) * ce_term * G.nhat[i];
+        }
+        gs[0] += gsv[0] * a.ds_de[0] + gsv[1] * a.ds_de[1] + gsv[2] * a.ds_de[2];
+        gs[1] += gsv[0] * a.ds_da[0] + gsv[1] * a.ds_da[1] + gsv[2] * a.ds_da[2];
+        gs[2] += gsv[0];
+        gs[3] += gsv[1];
+        gs[4] += gsv[2];
+    }
+    // block reduction of the sun gradient
+    __shared__ double red[5][8];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double v = gs[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        if (v != 0.0) atomicAdd(a.grad_sun + threadIdx.x, v);
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static int g_sm_count = 0;
+
+int device_sm_count() {
+    if (g_sm_count == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            g_sm_count = n;
+        else
+            g_sm_count = 1;
+    }
+    return g_sm_count;
+}
+
+// Grid-stride kernels: one wave of resident blocks (occupancy x SMs), fewer
+// when there is not enough work.
+template <typename K>
+static int resident_grid(K kernel, int block, int64_t n_threads) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int64_t cap = (int64_t)device_sm_count() * per_sm;
+    int64_t want = (n_threads + block - 1) / block;
+    if (want < 1) want = 1;
+    return (int)(want < cap ? want : cap);
+}
+
+cudaError_t launch_dp_forward(const FwdArgs& a, int block, cudaStream_t s) {
+    int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
+    if (a.O.counters)
+        dp_forward_kernel<true><<<resident_grid(dp_forward_kernel<true>, block, n), block, 0, s>>>(a);
+    else
+        dp_forward_kernel<false><<<resident_grid(dp_forward_kernel<false>, block, n), block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uniform_forward(const FwdArgs& a, int block, cudaStream_t s) {
+    int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
+    if (a.O.counters)
+        uniform_forward_kernel<true><<<resident_grid(uniform_forward_kernel<true>, block, n), block, 0, s>>>(a);
+    else
+        uniform_forward_kernel<false><<<resident_grid(uniform_forward_kernel<false>, block, n), block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const BwdArgs& a, int block, cudaStream_t s) {
+    int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
+    backward_kernel<<<resident_grid(backward_kernel, block, n), block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ss

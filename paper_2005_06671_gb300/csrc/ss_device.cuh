@@ -1,0 +1,356 @@
+// Device-side building blocks shared by the forward (descent and uniform),
+// backward and batched kernels.
+//
+// Per ray, FP64 is used once to set up a local frame (Sec. 3.1 shadow ray
+// p + t s; the gnomonic tile mapping of Sec. 3.2 / Appendix, under which the
+// ray's texel image is the straight line u(t) = u_p + A t'/(1 + b t')); every
+// sample is then evaluated in float32:
+//
+//   t_j   = j * delta
+//   rise  = |p + t s| - |p| = t (2 rho sin_e + t) / (rho + sqrt(rho^2 + t (2 rho sin_e + t)))
+//   c_j   = ((h_p - h_ref) + rise - bilinear(H - h_ref)(u_j, v_j)) / t_j
+//
+// with rho = R + h_p and h_ref a texel value next to the origin, so no float32
+// quantity is ever of the size of R (|p + t s| - R in float32 at R = 1737 km
+// would carry ~0.1 m of rounding).  Sample positions are formed from an exact
+// integer part and a float32 fraction.  The same leaf function serves the
+// descent and the uniform kernel, so both see bit-identical sample values.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace ss {
+
+constexpr int kMaxLevels = 18;     // 2^17 > SS_MAX_DIM
+constexpr float kPosEps = 1e-3f;   // texel margin of footprint boxes
+constexpr float kGuardRel = 1.9073486328125e-06f;  // 2^-19 = 32 float32 unit roundoffs
+
+// Maximum mipmap as seen by a kernel; level 0 is the heightfield itself.
+struct Pyramid {
+    const float* ptr[kMaxLevels];
+    int64_t pitch[kMaxLevels];
+    int32_t levels;
+};
+
+// Scalar launch parameters of one (tile, sun) instance.
+struct Tile {
+    const float* h;
+    int64_t pitch;
+    int32_t nx, ny;
+    int32_t proj;
+    int32_t J;                 // floor(max_len / delta)
+    double g, R, cx, cy;       // texel size, radius, tile centre in texel coords
+    double sx, sy, sz;         // sun direction
+    double delta;              // sample spacing (m)
+    double inv_gR;             // 1 / (g R)
+    double alpha;              // sun angular radius
+    float delta_f;             // (float)delta
+    float alpha_f;
+};
+
+struct Rays {
+    int32_t mode;              // 0 grid, 1 list
+    int64_t n;
+    const float* uv;
+    const float* lift;
+};
+
+struct Outputs {
+    float* light;
+    int32_t* argmin;
+    float* cost;
+    int32_t* counters;
+};
+
+// FP64 per-ray geometry (setup, final re-evaluation, backward).
+struct Geom64 {
+    double up, vp;             // origin texel coordinates
+    double hp, href;           // origin height, reference texel height
+    double rho;                // R + h_p
+    double sin_e, cos_e;       // sun elevation over the radial normal at p
+    double nhat[3];            // radial unit normal at p
+    double Au, Av, b;          // u_j = u_p + Au * j/(1 + b j), same for v
+    int32_t oi0, oj0;          // origin bilinear base texel
+    double ow[4];              // origin bilinear weights (i0,j0),(i0+1,j0),(i0,j0+1),(i0+1,j0+1)
+};
+
+// float32 per-ray state of the hot loop.
+struct RayF {
+    int32_t iu0, iv0;          // integer part of the origin position
+    float fu0, fv0;            // fractional part
+    float au_hi, au_lo, av_hi, av_lo;  // per-sample slope split so that j*a_hi is exact
+    float au, av;              // (float) slopes
+    float b;                   // projective coefficient
+    float B;                   // 2 rho sin_e
+    float rho, rho2, inv_rho;
+    float X;                   // h_p - h_ref
+    float href;
+    float tv;                  // distance of the lowest ray point (sin_e < 0), else -1
+    float guard0;              // |X| + height span of the tile
+    float cos_e;
+    int32_t j_lo, j_hi;        // usable sample range (empty when j_lo > j_hi)
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double fetch_bilinear64(const float* __restrict__ h, int64_t pitch,
+                                                   int nx, int ny, double u, double v,
+                                                   int32_t* i0o, int32_t* j0o, double w[4]) {
+    int32_t i0 = (int32_t)floor(u), j0 = (int32_t)floor(v);
+    i0 = min(max(i0, 0), nx - 2);
+    j0 = min(max(j0, 0), ny - 2);
+    double fu = u - (double)i0, fv = v - (double)j0;
+    const float* r0 = h + (int64_t)j0 * pitch + i0;
+    double h00 = r0[0], h10 = r0[1], h01 = r0[pitch], h11 = r0[pitch + 1];
+    w[0] = (1.0 - fu) * (1.0 - fv);
+    w[1] = fu * (1.0 - fv);
+    w[2] = (1.0 - fu) * fv;
+    w[3] = fu * fv;
+    *i0o = i0;
+    *j0o = j0;
+    return w[0] * h00 + w[1] * h10 + w[2] * h01 + w[3] * h11;
+}
+
+// Split a into hi + lo with hi carrying at most 8 significant bits, so that
+// j * hi is exact in float32 for j < 2^16.
+__device__ __forceinline__ void split8(double a, float& hi, float& lo) {
+    float af = (float)a;
+    hi = __int_as_float(__float_as_int(af) & (int)0xFFFF0000u);
+    lo = (float)(a - (double)hi);
+}
+
+// Origin height (FP64) of ray r.
+__device__ __forceinline__ void ray_origin(const Tile& T, const Rays& R, int64_t r,
+                                           double& up, double& vp, double& hp, double& href,
+                                           int32_t& oi0, int32_t& oj0, double ow[4]) {
+    if (R.mode == 0) {
+        int64_t v = r / T.nx;
+        int64_t u = r - v * T.nx;
+        up = (double)u;
+        vp = (double)v;
+        float hv = T.h[v * T.pitch + u];
+        hp = hv;
+        href = hv;
+        oi0 = (int32_t)(u < T.nx - 2 ? u : T.nx - 2);
+        oj0 = (int32_t)(v < T.ny - 2 ? v : T.ny - 2);
+        ow[0] = ow[1] = ow[2] = ow[3] = 0.0;
+        ow[(u - oi0) + 2 * (v - oj0)] = 1.0;
+    } else {
+        up = (double)R.uv[2 * r];
+        vp = (double)R.uv[2 * r + 1];
+        hp = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, up, vp, &oi0, &oj0, ow);
+        href = (double)T.h[(int64_t)oj0 * T.pitch + oi0];
+        if (R.lift) hp += (double)R.lift[r];
+    }
+}
+
+// FP64 local frame of a ray whose origin is at texel coords (up, vp), height hp.
+__device__ __forceinline__ void geom64(const Tile& T, double up, double vp, double hp,
+                                       Geom64& G) {
+    double Xp = (up - T.cx) * T.g, Yp = (vp - T.cy) * T.g;
+    double m = sqrt(Xp * Xp + Yp * Yp + T.R * T.R);
+    double im = 1.0 / m;
+    G.up = up;
+    G.vp = vp;
+    G.hp = hp;
+    G.nhat[0] = Xp * im;
+    G.nhat[1] = Yp * im;
+    G.nhat[2] = T.R * im;
+    G.sin_e = (Xp * T.sx + Yp * T.sy + T.R * T.sz) * im;
+    G.cos_e = sqrt(fmax(0.0, 1.0 - G.sin_e * G.sin_e));
+    G.rho = T.R + hp;
+    double f = T.delta * m / G.rho;           // sample index -> t' along the ray
+    double k = f * T.inv_gR;
+    G.Au = k * (T.R * T.sx - T.sz * Xp);
+    G.Av = k * (T.R * T.sy - T.sz * Yp);
+    G.b = f * T.sz / T.R;
+}
+
+// tau(j) = j/(1 + b j); the inverse is j = tau/(1 - b tau).
+__device__ __forceinline__ double tau_to_j(double tau, double b) {
+    double den = 1.0 - b * tau;
+    return den > 0.0 ? tau / den : INFINITY;
+}
+
+// Usable sample range: texel image inside [0,nx-1]x[0,ny-1] (clip of the line
+// u_p + Au tau, v_p + Av tau against the box), intersected with [1, J].
+__device__ __forceinline__ void sample_range(const Tile& T, const Geom64& G, int32_t& j_lo,
+                                             int32_t& j_hi) {
+    double tlo = 0.0, thi = INFINITY;
+    bool empty = false;
+    const double p0[2] = { G.up, G.vp }, a[2] = { G.Au, G.Av };
+    const double hi[2] = { (double)(T.nx - 1), (double)(T.ny - 1) };
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (a[k] == 0.0) {
+            if (p0[k] < 0.0 || p0[k] > hi[k]) empty = true;
+        } else {
+            double ia = 1.0 / a[k];
+            double t1 = (0.0 - p0[k]) * ia, t2 = (hi[k] - p0[k]) * ia;
+            tlo = fmax(tlo, fmin(t1, t2));
+            thi = fmin(thi, fmax(t1, t2));
+        }
+    }
+    if (empty || !(thi >= tlo)) {
+        j_lo = 1;
+        j_hi = 0;
+        return;
+    }
+    double jl = tau_to_j(tlo, G.b), jh = tau_to_j(thi, G.b);
+    j_lo = (int32_t)fmax(1.0, ceil(jl));
+    j_hi = (int32_t)fmin((double)T.J, floor(jh));
+}
+
+__device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double href,
+                                          float span, RayF& r) {
+    double iu = floor(G.up), iv = floor(G.vp);
+    r.iu0 = (int32_t)iu;
+    r.iv0 = (int32_t)iv;
+    r.fu0 = (float)(G.up - iu);
+    r.fv0 = (float)(G.vp - iv);
+    split8(G.Au, r.au_hi, r.au_lo);
+    split8(G.Av, r.av_hi, r.av_lo);
+    r.au = (float)G.Au;
+    r.av = (float)G.Av;
+    r.b = (float)G.b;
+    r.B = (float)(2.0 * G.rho * G.sin_e);
+    r.rho = (float)G.rho;
+    r.rho2 = (float)(G.rho * G.rho);
+    r.inv_rho = (float)(1.0 / G.rho);
+    r.X = (float)(G.hp - href);
+    r.href = (float)href;
+    r.tv = G.sin_e < 0.0 ? (float)(-G.rho * G.sin_e) : -1.0f;
+    r.guard0 = fabsf(r.X) + span;
+    r.cos_e = (float)G.cos_e;
+    sample_range(T, G, r.j_lo, r.j_hi);
+}
+
+// ------------------------------------------------------------ float32 leaf
+struct Pos {
+    int32_t i;
+    float f;
+};
+
+// Texel coordinate of sample j along one axis: integer part exact, fraction
+// accurate to ~1e-7 texel.  Base clamped to [0, n-2] (fraction absorbs it).
+__device__ __forceinline__ Pos axis_pos(int32_t i0, float f0, float a_hi, float a_lo, float a,
+                                        float corr, float jf, int32_t n) {
+    float p = jf * a_hi;                 // exact
+    float kp = floorf(p);
+    float fp = p - kp;                   // exact
+    float s = f0 + fp + fmaf(jf, a_lo, -a * corr);
+    float fs = floorf(s);
+    int32_t i = i0 + (int32_t)kp + (int32_t)fs;
+    float f = s - fs;
+    int32_t ic = min(max(i, 0), n - 2);
+    f += (float)(i - ic);
+    Pos P;
+    P.i = ic;
+    P.f = f;
+    return P;
+}
+
+__device__ __forceinline__ float corr_of(const RayF& r, float jf) {
+    float jb = jf * r.b;
+    return __fdividef(jf * jb, 1.0f + jb);   // j - j/(1 + b j)
+}
+
+// |p + t s| - |p| without cancellation.
+__device__ __forceinline__ float rise_of(const RayF& r, float t) {
+    float w = t * (r.B + t);
+    return w / (r.rho + sqrtf(fmaf(r.rho, r.rho, w)));
+}
+
+// upper bound of |rise(t)| without a square root
+__device__ __forceinline__ float rise_bound(const RayF& r, float t) {
+    return fabsf(t * (r.B + t)) * r.inv_rho;
+}
+
+__device__ __forceinline__ float bilinear_rel(const float* __restrict__ h, int64_t pitch,
+                                              const Pos& pu, const Pos& pv, float href) {
+    const float* p = h + (int64_t)pv.i * pitch + pu.i;
+    float d00 = __ldg(p) - href, d10 = __ldg(p + 1) - href;
+    float d01 = __ldg(p + pitch) - href, d11 = __ldg(p + pitch + 1) - href;
+    float top = fmaf(pu.f, d10 - d00, d00);
+    float bot = fmaf(pu.f, d11 - d01, d01);
+    return fmaf(pv.f, bot - top, top);
+}
+
+// Cost of sample j (float32); identical in every kernel.
+__device__ __forceinline__ float leaf_cost(const Tile& T, const RayF& r, int32_t j,
+                                           float* rise_out = nullptr) {
+    float jf = (float)j;
+    float corr = corr_of(r, jf);
+    Pos pu = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, corr, jf, T.nx);
+    Pos pv = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, corr, jf, T.ny);
+    float t = jf * T.delta_f;
+    float rise = rise_of(r, t);
+    if (rise_out) *rise_out = rise;
+    float hb = bilinear_rel(T.h, T.pitch, pu, pv, r.href);
+    return ((r.X + rise) - hb) / t;
+}
+
+// Lower bound of every leaf_cost(j), ja <= j <= jb, through the maximum mipmap:
+// M = max of the heights under the footprint box of the samples (Eq. optimumk2:
+// the clearance over an interval is at least the ray's lowest height minus
+// the maximum terrain height below it).  guard = 2^-19 (|X| + |rise| + |M -
+// h_ref| + span) covers every float32 rounding of leaf_cost and of this bound.
+__device__ __forceinline__ float node_bound(const Tile& T, const Pyramid& P,
+                                            const float* const* lev_ptr,
+                                            const int64_t* lev_pitch, const RayF& r,
+                                            int32_t ja, int32_t jb) {
+    float fa = (float)ja, fb = (float)jb;
+    float ca = corr_of(r, fa), cb = corr_of(r, fb);
+    Pos ua = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, ca, fa, T.nx);
+    Pos ub = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, cb, fb, T.nx);
+    Pos va = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, ca, fa, T.ny);
+    Pos vb = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, cb, fb, T.ny);
+    int32_t xa0 = ua.i - (ua.f < kPosEps ? 1 : 0), xb0 = ub.i - (ub.f < kPosEps ? 1 : 0);
+    int32_t xa1 = ua.i + (ua.f + kPosEps >= 1.0f ? 2 : 1), xb1 = ub.i + (ub.f + kPosEps >= 1.0f ? 2 : 1);
+    int32_t ya0 = va.i - (va.f < kPosEps ? 1 : 0), yb0 = vb.i - (vb.f < kPosEps ? 1 : 0);
+    int32_t ya1 = va.i + (va.f + kPosEps >= 1.0f ? 2 : 1), yb1 = vb.i + (vb.f + kPosEps >= 1.0f ? 2 : 1);
+    int32_t x0 = max(min(xa0, xb0), 0), x1 = min(max(xa1, xb1), T.nx - 1);
+    int32_t y0 = max(min(ya0, yb0), 0), y1 = min(max(ya1, yb1), T.ny - 1);
+    int32_t e = max(x1 - x0, y1 - y0);
+    int32_t m = e <= 1 ? 0 : 31 - __clz(e);
+    if (((x1 >> m) - (x0 >> m)) > 1 || ((y1 >> m) - (y0 >> m)) > 1) ++m;
+    m = min(m, P.levels - 1);
+    const float* lp = lev_ptr[m];
+    int64_t pm = lev_pitch[m];
+    int32_t xa = x0 >> m, xb = x1 >> m, ya = y0 >> m, yb = y1 >> m;
+    float M = fmaxf(fmaxf(__ldg(lp + (int64_t)ya * pm + xa), __ldg(lp + (int64_t)ya * pm + xb)),
+                    fmaxf(__ldg(lp + (int64_t)yb * pm + xa), __ldg(lp + (int64_t)yb * pm + xb)));
+    float Mrel = M - r.href;
+    float ta = fa * T.delta_f, tb = fb * T.delta_f;
+    float tmin = (r.tv > ta) ? fminf(r.tv, tb) : ta;
+    float rmin = rise_of(r, tmin);
+    float guard = kGuardRel * (r.guard0 + fabsf(Mrel) + rise_bound(r, tb) + fabsf(rmin));
+    float num = ((r.X + rmin) - Mrel) - guard;
+    return num / (num >= 0.0f ? tb : ta);
+}
+
+// ------------------------------------------------------ FP64 re-evaluation
+__device__ __forceinline__ double leaf_cost64(const Tile& T, const Geom64& G, int32_t j,
+                                              double* U = nullptr, double* V = nullptr) {
+    double jd = (double)j;
+    double tau = jd / (1.0 + G.b * jd);
+    double u = G.up + G.Au * tau, v = G.vp + G.Av * tau;
+    if (U) *U = u;
+    if (V) *V = v;
+    int32_t i0, j0;
+    double w[4];
+    double hb = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, u, v, &i0, &j0, w);
+    double t = jd * T.delta;
+    double wq = t * (2.0 * G.rho * G.sin_e + t);
+    double rise = wq / (G.rho + sqrt(G.rho * G.rho + wq));
+    return ((G.hp - hb) + rise) / t;
+}
+
+__device__ __forceinline__ double disc_light64(double d) {
+    if (d <= -1.0) return 0.0;
+    if (d >= 1.0) return 1.0;
+    return (M_PI - acos(d) + d * sqrt(1.0 - d * d)) / M_PI;
+}
+
+}  // namespace ss

@@ -1,0 +1,53 @@
+// Internal host-side interface between the C ABI (api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ss_device.cuh"
+
+namespace ss {
+
+// Layout of the maximum-mipmap buffer (levels 1..L-1, then two stats floats).
+struct MipLayout {
+    int32_t levels;                 // including level 0
+    int32_t w[kMaxLevels], h[kMaxLevels];
+    int64_t pitch[kMaxLevels];      // level 0: not used (heights keep their own pitch)
+    int64_t offset[kMaxLevels];     // elements from the buffer start (level >= 1)
+    int64_t stats_offset;           // (global max, global min)
+    int64_t total_elems;
+};
+
+bool mip_layout(int32_t nx, int32_t ny, MipLayout* L);
+
+struct FwdArgs {
+    Tile T;
+    Pyramid P;
+    Rays R;
+    Outputs O;
+    const float* stats;   // device: (global max, global min) of the heights
+    int32_t kleaf;
+    uint32_t flags;
+};
+
+struct BwdArgs {
+    Tile T;
+    Rays R;
+    const int32_t* argmin;
+    const float* grad_light;
+    float* grad_h;
+    int64_t grad_pitch;
+    double* grad_sun;
+    double ds_de[3], ds_da[3];
+};
+
+cudaError_t launch_build_maxmip(const float* h, int32_t nx, int32_t ny, int64_t pitch,
+                                float* mip, const MipLayout& L, cudaStream_t s);
+cudaError_t launch_dp_forward(const FwdArgs& a, int block, cudaStream_t s);
+cudaError_t launch_uniform_forward(const FwdArgs& a, int block, cudaStream_t s);
+cudaError_t launch_backward(const BwdArgs& a, int block, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace ss

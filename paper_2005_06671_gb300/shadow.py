@@ -1,0 +1,234 @@
+"""PyTorch-facing binding of libsoftshadow (device memory and streams only).
+
+Each ``ss_*`` function marshals tensors into the C ABI of the same name
+(include/softshadow.h) and enqueues the work on the current CUDA stream.
+``ShadowFn`` wraps forward + backward as a ``torch.autograd.Function``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _abi
+from ._abi import (SSHeightfield, SSOutputs, SSParams, SSRays, SSSun, check,
+                   SS_FLAG_COUNT_SAMPLES, SS_FLAG_NO_EARLY_EXIT)
+
+PROJ = {"gnomonic": _abi.SS_PROJ_GNOMONIC, "polar_stereo": _abi.SS_PROJ_POLAR_STEREO}
+
+
+@dataclass
+class Heightfield:
+    """A float32 CUDA tensor [ny, nx] of heights (m) with its mapping to the sphere."""
+    h: torch.Tensor
+    texel_m: float
+    radius_m: float
+    projection: str = "gnomonic"
+
+    def c(self):
+        h = self.h
+        if not (h.is_cuda and h.dtype == torch.float32 and h.dim() == 2 and h.stride(1) == 1):
+            raise ValueError("heights must be a 2-D float32 CUDA tensor with unit column stride")
+        return SSHeightfield(h.data_ptr(), h.shape[1], h.shape[0], h.stride(0),
+                             float(self.texel_m), float(self.radius_m), PROJ[self.projection])
+
+    @property
+    def shape(self):
+        return tuple(self.h.shape)
+
+
+@dataclass
+class Sun:
+    elevation: float
+    azimuth: float
+    angular_radius: float = math.radians(0.2665)
+
+    def c(self):
+        return SSSun(float(self.elevation), float(self.azimuth), float(self.angular_radius))
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def version():
+    return _abi.lib().ss_version().decode()
+
+
+# ------------------------------------------------------------------ mipmap
+def maxmip_bytes(nx, ny):
+    return int(_abi.lib().ss_maxmip_bytes(nx, ny))
+
+
+def maxmip_layout(nx, ny):
+    """[(width, height, pitch, offset_elems)] for levels 1..L-1, then the stats block."""
+    L = _abi.lib()
+    n = int(L.ss_maxmip_levels(nx, ny))
+    out = []
+    for lvl in range(1, n + 1):
+        w, h, p, o = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        check(L.ss_maxmip_level_info(nx, ny, lvl, ctypes.byref(w), ctypes.byref(h),
+                                     ctypes.byref(p), ctypes.byref(o)), "ss_maxmip_level_info")
+        out.append((w.value, h.value, p.value, o.value))
+    return out
+
+
+def maxmip_views(mip, nx, ny):
+    """Views of levels 1..L-1 of a mip buffer as 2-D tensors (padding excluded)."""
+    views = []
+    lay = maxmip_layout(nx, ny)
+    for (w, h, p, o) in lay[:-1]:
+        views.append(mip[o:o + p * h].view(h, p)[:, :w])
+    return views
+
+
+def maxmip_stats(mip, nx, ny):
+    """(global max, global min) tensor view stored after the levels."""
+    w, h, p, o = maxmip_layout(nx, ny)[-1]
+    return mip[o:o + 2]
+
+
+def ss_build_maxmip(hf: Heightfield, mip=None, stream=None):
+    ny, nx = hf.shape
+    if mip is None:
+        mip = torch.empty(maxmip_bytes(nx, ny) // 4, dtype=torch.float32, device=hf.h.device)
+    check(_abi.lib().ss_build_maxmip(ctypes.byref(hf.c()), _ptr(mip), _stream_ptr(stream)),
+          "ss_build_maxmip")
+    return mip
+
+
+# ----------------------------------------------------------------- forward
+def _params(max_len_m, step_texels, flags, block_threads, leaf_level):
+    return SSParams(float(max_len_m), float(step_texels), int(flags), int(block_threads),
+                    int(leaf_level), 0)
+
+
+def _rays(hf, uv, lift):
+    if uv is None:
+        ny, nx = hf.shape
+        return SSRays(_abi.SS_RAYS_GRID, 0, None, None), nx * ny
+    if not (uv.is_cuda and uv.dtype == torch.float32 and uv.is_contiguous() and uv.shape[-1] == 2):
+        raise ValueError("uv must be a contiguous float32 CUDA tensor [n, 2]")
+    if lift is not None and not (lift.is_cuda and lift.dtype == torch.float32 and lift.is_contiguous()):
+        raise ValueError("lift must be a contiguous float32 CUDA tensor [n]")
+    n = uv.numel() // 2
+    return SSRays(_abi.SS_RAYS_LIST, n, uv.data_ptr(), None if lift is None else lift.data_ptr()), n
+
+
+def _outputs(n, device, want_cost, count, out):
+    if out is None:
+        out = {}
+    light = out.get("light")
+    if light is None:
+        light = torch.empty(n, dtype=torch.float32, device=device)
+    argmin = out.get("argmin")
+    if argmin is None:
+        argmin = torch.empty(n, dtype=torch.int32, device=device)
+    cost = out.get("cost")
+    if cost is None and want_cost:
+        cost = torch.empty(n, dtype=torch.float32, device=device)
+    counters = out.get("counters")
+    if counters is None and count:
+        counters = torch.empty((n, 2), dtype=torch.int32, device=device)
+    c = SSOutputs(light.data_ptr(), argmin.data_ptr(), None if cost is None else cost.data_ptr(),
+                  None if counters is None else counters.data_ptr())
+    return c, dict(light=light, argmin=argmin, cost=cost, counters=counters)
+
+
+def _forward(fn_name, hf, mip, sun, max_len_m, step_texels, uv, lift, flags, block_threads,
+             leaf_level, want_cost, out, stream):
+    rays, n = _rays(hf, uv, lift)
+    count = bool(flags & SS_FLAG_COUNT_SAMPLES)
+    oc, res = _outputs(n, hf.h.device, want_cost, count, out)
+    prm = _params(max_len_m, step_texels, flags, block_threads, leaf_level)
+    fn = getattr(_abi.lib(), fn_name)
+    check(fn(ctypes.byref(hf.c()), _ptr(mip), ctypes.byref(rays), ctypes.byref(sun.c()),
+             ctypes.byref(prm), ctypes.byref(oc), _stream_ptr(stream)), fn_name)
+    return res
+
+
+def ss_shadow_forward(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
+                      lift=None, count_samples=False, block_threads=0, leaf_level=-1,
+                      want_cost=True, out=None, stream=None):
+    """Exact max-mip descent.  Returns dict(light, argmin, cost, counters)."""
+    flags = SS_FLAG_COUNT_SAMPLES if count_samples else 0
+    return _forward("ss_shadow_forward", hf, mip, sun, max_len_m, step_texels, uv, lift, flags,
+                    block_threads, leaf_level, want_cost, out, stream)
+
+
+def ss_shadow_uniform(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
+                      lift=None, count_samples=False, early_exit=True, block_threads=0,
+                      want_cost=True, out=None, stream=None):
+    """Uniform stepping over every sample (exact early exit unless disabled)."""
+    flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (0 if early_exit else SS_FLAG_NO_EARLY_EXIT)
+    return _forward("ss_shadow_uniform", hf, mip, sun, max_len_m, step_texels, uv, lift, flags,
+                    block_threads, -1, want_cost, out, stream)
+
+
+# ---------------------------------------------------------------- backward
+def ss_shadow_backward(hf: Heightfield, sun: Sun, max_len_m, argmin, grad_light, step_texels=0.5,
+                       uv=None, lift=None, grad_h=None, grad_sun=None, block_threads=0,
+                       stream=None):
+    """Accumulates dL/dh into grad_h [ny, nx] (float32) and dL/d(elev, az, s_x, s_y, s_z)
+    into grad_sun (float64 [5]); allocates zeroed ones when not given."""
+    rays, n = _rays(hf, uv, lift)
+    if grad_h is None:
+        grad_h = torch.zeros_like(hf.h)
+    if grad_h.stride() != hf.h.stride() or grad_h.shape != hf.h.shape:
+        raise ValueError("grad_h must have the heights' shape and strides")
+    if grad_sun is None:
+        grad_sun = torch.zeros(5, dtype=torch.float64, device=hf.h.device)
+    argmin = argmin.contiguous()
+    grad_light = grad_light.to(torch.float32).contiguous()
+    prm = _params(max_len_m, step_texels, 0, block_threads, -1)
+    check(_abi.lib().ss_shadow_backward(ctypes.byref(hf.c()), ctypes.byref(rays),
+                                        ctypes.byref(sun.c()), ctypes.byref(prm),
+                                        _ptr(argmin), _ptr(grad_light), _ptr(grad_h),
+                                        _ptr(grad_sun), _stream_ptr(stream)),
+          "ss_shadow_backward")
+    return grad_h, grad_sun
+
+
+# ---------------------------------------------------------------- autograd
+class ShadowFn(torch.autograd.Function):
+    """light = shadow(h, sun_angles) with a hand-written adjoint.
+
+    Inputs: h [ny, nx] float32 CUDA, sun_angles float64 tensor [2] =
+    (elevation, azimuth) in rad.  Non-tensor arguments: texel_m, radius_m,
+    alpha, max_len_m, step_texels.  Output: light [ny*nx] (grid mode).
+    The gradient is a subgradient of the per-ray minimum (taken at the argmin).
+    """
+
+    @staticmethod
+    def forward(ctx, h, sun_angles, texel_m, radius_m, alpha, max_len_m, step_texels=0.5):
+        e, a = (float(x) for x in sun_angles.detach().cpu().tolist())
+        hf = Heightfield(h.detach().contiguous(), texel_m, radius_m)
+        sun = Sun(e, a, alpha)
+        mip = ss_build_maxmip(hf)
+        res = ss_shadow_forward(hf, mip, sun, max_len_m, step_texels, want_cost=False)
+        ctx.save_for_backward(hf.h, res["argmin"])
+        ctx.geom = (texel_m, radius_m, alpha, max_len_m, step_texels, e, a)
+        ctx.sun_dtype = sun_angles.dtype
+        ctx.sun_device = sun_angles.device
+        return res["light"]
+
+    @staticmethod
+    def backward(ctx, grad_light):
+        h, argmin = ctx.saved_tensors
+        texel_m, radius_m, alpha, max_len_m, step_texels, e, a = ctx.geom
+        hf = Heightfield(h, texel_m, radius_m)
+        gh, gs = ss_shadow_backward(hf, Sun(e, a, alpha), max_len_m, argmin,
+                                    grad_light.contiguous(), step_texels)
+        g_sun = gs[:2].to(device=ctx.sun_device, dtype=ctx.sun_dtype)
+        return gh, g_sun, None, None, None, None, None
+
+
+def shadow(h, sun_angles, texel_m, radius_m, alpha, max_len_m, step_texels=0.5):
+    return ShadowFn.apply(h, sun_angles, texel_m, radius_m, alpha, max_len_m, step_texels)

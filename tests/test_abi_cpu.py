@@ -1,0 +1,109 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol that
+include/*.h declares, and rejects bad arguments on the host before any launch.
+(No call here reaches a kernel: each one fails validation first.)"""
+import ctypes
+import math
+
+import pytest
+
+from paper_2005_06671_gb300 import _abi
+from paper_2005_06671_gb300._abi import (SSHeightfield, SSOutputs, SSParams, SSRays, SSSun)
+
+FAKE = 0x10000   # never dereferenced: every call below fails validation first
+
+
+def test_library_exports_every_header_symbol():
+    lib = _abi.lib()
+    names = _abi.header_symbols()
+    assert "ss_shadow_forward" in names and "ss_build_maxmip" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_layout_queries():
+    lib = _abi.lib()
+    for s in range(8):
+        assert lib.ss_status_string(s)
+    assert lib.ss_maxmip_levels(4096, 4096) == 13
+    assert lib.ss_maxmip_levels(256, 256) == 9
+    assert lib.ss_maxmip_levels(1, 1) == 1
+    assert lib.ss_maxmip_levels(0, 5) == 0
+    assert lib.ss_maxmip_bytes(0, 5) == 0
+    # levels 1.. of 4096^2: 4^-1 + 4^-2 + ... of the tile, plus alignment and stats
+    b = lib.ss_maxmip_bytes(4096, 4096)
+    assert 4096 * 4096 * 4 // 3 <= b <= 4096 * 4096 * 4 // 3 + 64 * 1024
+    w, h, p, o = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64())
+    assert lib.ss_maxmip_level_info(1000, 777, 1, ctypes.byref(w), ctypes.byref(h),
+                                    ctypes.byref(p), ctypes.byref(o)) == 0
+    assert (w.value, h.value) == (500, 389) and p.value % 4 == 0 and o.value % 64 == 0
+    assert lib.ss_maxmip_level_info(1000, 777, 99, None, None, None, None) == 1
+
+
+def _good():
+    hf = SSHeightfield(FAKE, 64, 64, 64, 10.0, 1737.4e3, 0)
+    sun = SSSun(math.radians(1.0), 0.5, math.radians(0.2665))
+    prm = SSParams(1000.0, 0.5, 0, 0, -1, 0)
+    rays = SSRays(0, 0, None, None)
+    out = SSOutputs(FAKE, FAKE, None, None)
+    return hf, sun, prm, rays, out
+
+
+def _fwd(hf, sun, prm, rays, out, mip=FAKE):
+    lib = _abi.lib()
+    return lib.ss_shadow_forward(ctypes.byref(hf) if hf is not None else None,
+                                 ctypes.c_void_p(mip) if mip else None,
+                                 ctypes.byref(rays), ctypes.byref(sun), ctypes.byref(prm),
+                                 ctypes.byref(out), None)
+
+
+@pytest.mark.parametrize("mutate,expect", [
+    (lambda a: a.__setitem__(0, None), 1),
+    (lambda a: setattr(a[0], "h", None), 1),
+    (lambda a: setattr(a[0], "nx", 1), 2),
+    (lambda a: setattr(a[0], "ny", 70000), 2),
+    (lambda a: setattr(a[0], "pitch", 10), 2),
+    (lambda a: setattr(a[0], "texel_m", -1.0), 1),
+    (lambda a: setattr(a[0], "radius_m", float("nan")), 1),
+    (lambda a: setattr(a[0], "projection", 5), 1),
+    (lambda a: setattr(a[1], "elevation_rad", 2.0), 1),
+    (lambda a: setattr(a[1], "angular_radius_rad", 0.0), 1),
+    (lambda a: setattr(a[1], "azimuth_rad", float("inf")), 1),
+    (lambda a: setattr(a[2], "max_len_m", 0.0), 1),
+    (lambda a: setattr(a[2], "max_len_m", 1e9), 2),
+    (lambda a: setattr(a[2], "step_texels", -0.5), 1),
+    (lambda a: setattr(a[2], "flags", 0x80), 1),
+    (lambda a: setattr(a[2], "block_threads", 100), 1),
+    (lambda a: setattr(a[2], "leaf_level", 40), 1),
+    (lambda a: setattr(a[2], "reserved", 1), 1),
+    (lambda a: setattr(a[3], "mode", 7), 1),
+    (lambda a: (setattr(a[3], "mode", 1), setattr(a[3], "n", -3)), 2),
+    (lambda a: (setattr(a[3], "mode", 1), setattr(a[3], "n", 5)), 1),
+    (lambda a: setattr(a[4], "light", None), 1),
+    (lambda a: setattr(a[4], "argmin", None), 1),
+    (lambda a: setattr(a[2], "flags", 1), 1),        # counters requested but NULL
+    (lambda a: a.__setitem__(5, 0), 1),              # NULL mip
+    (lambda a: setattr(a[0], "projection", 1), 7),   # valid, not in this build's kernels
+])
+def test_forward_rejects_bad_arguments(mutate, expect):
+    args = list(_good()) + [FAKE]
+    mutate(args)
+    hf, sun, prm, rays, out, mip = args
+    assert _fwd(hf, sun, prm, rays, out, mip) == expect
+
+
+def test_other_entry_points_reject_bad_arguments():
+    lib = _abi.lib()
+    hf, sun, prm, rays, out = _good()
+    assert lib.ss_build_maxmip(None, ctypes.c_void_p(FAKE), None) == 1
+    assert lib.ss_build_maxmip(ctypes.byref(hf), None, None) == 1
+    bad = SSHeightfield(FAKE, 0, 4, 4, 10.0, 1.0, 0)
+    assert lib.ss_build_maxmip(ctypes.byref(bad), ctypes.c_void_p(FAKE), None) == 2
+    assert lib.ss_shadow_uniform(ctypes.byref(hf), None, ctypes.byref(rays), ctypes.byref(sun),
+                                 ctypes.byref(prm), ctypes.byref(out), None) == 1
+    assert lib.ss_shadow_backward(ctypes.byref(hf), ctypes.byref(rays), ctypes.byref(sun),
+                                  ctypes.byref(prm), None, ctypes.c_void_p(FAKE),
+                                  ctypes.c_void_p(FAKE), ctypes.c_void_p(FAKE), None) == 1
+    prm.max_len_m = -1.0
+    assert lib.ss_shadow_backward(ctypes.byref(hf), ctypes.byref(rays), ctypes.byref(sun),
+                                  ctypes.byref(prm), ctypes.c_void_p(FAKE), ctypes.c_void_p(FAKE),
+                                  ctypes.c_void_p(FAKE), ctypes.c_void_p(FAKE), None) == 1

@@ -1,0 +1,267 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, on the same seeded inputs.
+
+Bars: light within 1e-5 absolute; argmin equal except at ties within 1e-6 rad;
+mipmap levels bit-exact; descent and uniform stepping bit-identical (same
+argmin and same float32 cost on every ray).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import make_instance, lunar_tile, random_origins, MOON_RADIUS_M
+
+import paper_2005_06671_gb300 as ss
+from _parity import compare_to_oracle, random_ids, LIGHT_TOL
+
+pytestmark = pytest.mark.gpu
+R = MOON_RADIUS_M
+ALPHA = math.radians(0.2665)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run(h, g, sun, lmax, step=0.5, method="dp", uv=None, lift=None, count=False,
+         early_exit=True, hpad=0, leaf_level=-1, block_threads=0):
+    ny, nx = h.shape
+    if hpad:
+        store = torch.full((ny, nx + hpad), float("nan"), device="cuda")
+        store[:, :nx] = _dev(h)
+        ht = store[:, :nx]
+    else:
+        ht = _dev(h)
+    hf = ss.Heightfield(ht, g, R)
+    mip = ss.ss_build_maxmip(hf)
+    s = ss.Sun(*sun)
+    uvt = None if uv is None else _dev(uv)
+    lt = None if lift is None else _dev(lift)
+    if method == "dp":
+        res = ss.ss_shadow_forward(hf, mip, s, lmax, step, uv=uvt, lift=lt, count_samples=count,
+                                   leaf_level=leaf_level, block_threads=block_threads)
+    else:
+        res = ss.ss_shadow_uniform(hf, mip, s, lmax, step, uv=uvt, lift=lt, count_samples=count,
+                                   early_exit=early_exit, block_threads=block_threads)
+    torch.cuda.synchronize()
+    return {k: (None if v is None else v.cpu().numpy()) for k, v in res.items()}
+
+
+# --------------------------------------------------------------- mipmap
+@pytest.mark.parametrize("shape,pad", [((256, 256), 0), ((4096, 4096), 0), ((777, 1000), 0),
+                                       ((31, 65), 3), ((2, 2), 0), ((1, 9), 0), ((130, 67), 1)])
+def test_maxmip_bit_exact(shape, pad):
+    ny, nx = shape
+    rng = np.random.default_rng(nx * 7 + ny)
+    h = (rng.normal(size=shape) * 900).astype(np.float32)
+    ref = oracle.maxmip(h)
+    if pad:
+        store = torch.zeros((ny, nx + pad), device="cuda")
+        store[:, :nx] = _dev(h)
+        ht = store[:, :nx]
+    else:
+        ht = _dev(h)
+    hf = ss.Heightfield(ht, 10.0, R)
+    mip = ss.ss_build_maxmip(hf)
+    torch.cuda.synchronize()
+    views = ss.maxmip_views(mip, nx, ny)
+    assert len(views) == len(ref) - 1
+    for lvl, v in enumerate(views, start=1):
+        assert np.array_equal(v.cpu().numpy(), ref[lvl]), lvl
+    st = ss.maxmip_stats(mip, nx, ny).cpu().numpy()
+    assert st[0] == h.max() and st[1] == h.min()
+
+
+# ------------------------------------------------------- tiny, full grid
+@pytest.mark.parametrize("method", ["dp", "uniform"])
+def test_tiny_full_grid_vs_oracle(method):
+    inst = make_instance("tiny")
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][0]
+    sun = (elev, az, inst["alpha"])
+    out = _run(h, g, sun, inst["lmax"], method=method)
+    ids = np.arange(h.size)
+    st = compare_to_oracle(h, g, R, sun, inst["lmax"], 0.5, out["light"], out["argmin"],
+                           out["cost"], ray_ids=ids)
+    assert st["penumbra"] > 100
+
+
+def _pair(h, g, sun, lmax, step=0.5, **kw):
+    a = _run(h, g, sun, lmax, step, method="dp", **kw)
+    b = _run(h, g, sun, lmax, step, method="uniform", **kw)
+    return a, b
+
+
+@pytest.mark.parametrize("name,n", [("tiny", None), ("diff", 384), ("mid", 512)])
+def test_descent_equals_uniform_bitwise(name, n):
+    inst = make_instance(name, n=n)
+    h, g = inst["h"], inst["g"]
+    for (elev, az) in inst["suns"]:
+        sun = (elev, az, inst["alpha"])
+        a, b = _pair(h, g, sun, inst["lmax"])
+        c = _run(h, g, sun, inst["lmax"], method="uniform", early_exit=False)
+        assert np.array_equal(a["argmin"], b["argmin"])
+        assert np.array_equal(a["cost"].view(np.uint32), b["cost"].view(np.uint32))
+        assert np.array_equal(a["light"].view(np.uint32), b["light"].view(np.uint32))
+        assert np.array_equal(b["argmin"], c["argmin"])
+        assert np.array_equal(b["cost"].view(np.uint32), c["cost"].view(np.uint32))
+
+
+@pytest.mark.parametrize("leaf_level,block", [(0, 64), (1, 128), (5, 256), (8, 96)])
+def test_descent_tuning_knobs_do_not_change_results(leaf_level, block):
+    inst = make_instance("diff", n=256)
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][2]
+    sun = (elev, az, inst["alpha"])
+    ref = _run(h, g, sun, inst["lmax"], method="uniform")
+    out = _run(h, g, sun, inst["lmax"], leaf_level=leaf_level, block_threads=block)
+    assert np.array_equal(out["argmin"], ref["argmin"])
+    assert np.array_equal(out["cost"].view(np.uint32), ref["cost"].view(np.uint32))
+
+
+# ------------------------------------------------------------- list mode
+@pytest.mark.parametrize("method", ["dp", "uniform"])
+def test_list_mode_with_lift_vs_oracle(method):
+    inst = make_instance("tiny")
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][0]
+    sun = (elev, az, inst["alpha"])
+    n = 3000
+    uv = random_origins(n, 256, 256, seed=77)
+    lift = np.random.default_rng(78).uniform(0, 40, n).astype(np.float32)
+    lift[:500] = 0.0
+    out = _run(h, g, sun, inst["lmax"], method=method, uv=uv, lift=lift)
+    compare_to_oracle(h, g, R, sun, inst["lmax"], 0.5, out["light"], out["argmin"],
+                      out["cost"], uv=uv, lift=lift)
+
+
+# ---------------------------------------------- differentiable config, 4 suns
+def test_diff_config_sampled_vs_oracle():
+    inst = make_instance("diff")
+    h, g = inst["h"], inst["g"]
+    for k, (elev, az) in enumerate(inst["suns"]):
+        sun = (elev, az, inst["alpha"])
+        out = _run(h, g, sun, inst["lmax"])
+        ids = random_ids(h.size, 2500, seed=100 + k)
+        compare_to_oracle(h, g, R, sun, inst["lmax"], 0.5, out["light"][ids],
+                          out["argmin"][ids], out["cost"][ids], ray_ids=ids)
+
+
+# ------------------------------------- mid config at full size (bench launch)
+def test_mid_full_size_sampled_vs_oracle_and_uniform():
+    inst = make_instance("mid")
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][0]
+    sun = (elev, az, inst["alpha"])
+    a = _run(h, g, sun, inst["lmax"], count=True)
+    ids = random_ids(h.size, 4000, seed=4096)
+    st = compare_to_oracle(h, g, R, sun, inst["lmax"], 0.5, a["light"][ids], a["argmin"][ids],
+                           a["cost"][ids], ray_ids=ids)
+    b = _run(h, g, sun, inst["lmax"], method="uniform", count=True)
+    assert np.array_equal(a["argmin"], b["argmin"])
+    assert np.array_equal(a["cost"].view(np.uint32), b["cost"].view(np.uint32))
+    # the descent evaluates far fewer leaf samples than uniform stepping
+    assert a["counters"][:, 1].sum() * 5 < b["counters"][:, 1].sum()
+    print("mid parity", st, "mean bound probes", a["counters"][:, 0].mean(),
+          "mean leaf samples dp/uniform", a["counters"][:, 1].mean(), b["counters"][:, 1].mean())
+
+
+# ------------------------------------------------------------- edge cases
+def test_edge_cases():
+    h = lunar_tile(97, 15.0, seed=9, amplitude=400.0, n_craters=6, ny=61)
+    sun = (math.radians(1.3), math.radians(211.0), ALPHA)
+    # odd non-square tile, padded rows, non-default step
+    for method in ("dp", "uniform"):
+        out = _run(h, 15.0, sun, 3000.0, step=0.37, method=method, hpad=5)
+        compare_to_oracle(h, 15.0, R, sun, 3000.0, 0.37, out["light"], out["argmin"],
+                          out["cost"], ray_ids=np.arange(h.size))
+    # max_len shorter than one step: no sample at all
+    out = _run(h, 15.0, sun, 5.0)
+    assert np.all(out["light"] == 1.0) and np.all(out["argmin"] == -1)
+    assert np.all(np.isinf(out["cost"]))
+    # sun below the horizon
+    low = (math.radians(-1.0), 0.4, ALPHA)
+    out = _run(h, 15.0, low, 2000.0)
+    compare_to_oracle(h, 15.0, R, low, 2000.0, 0.5, out["light"], out["argmin"], out["cost"],
+                      ray_ids=np.arange(h.size))
+    # the longest ray the ABI allows (65535 samples) on a small tile
+    out = _run(h, 15.0, sun, 65535 * 7.5, step=0.5)
+    ids = random_ids(h.size, 300, seed=5)
+    compare_to_oracle(h, 15.0, R, sun, 65535 * 7.5, 0.5, out["light"][ids], out["argmin"][ids],
+                      out["cost"][ids], ray_ids=ids)
+    # empty ray list
+    hf = ss.Heightfield(_dev(h), 15.0, R)
+    mip = ss.ss_build_maxmip(hf)
+    res = ss.ss_shadow_forward(hf, mip, ss.Sun(*sun), 2000.0,
+                               uv=torch.zeros((0, 2), device="cuda"))
+    assert res["light"].numel() == 0
+
+
+def test_flat_terrain_closed_form_on_gpu():
+    nx, ny, g, h0 = 65, 48, 20.0, 123.25
+    h = np.full((ny, nx), h0, np.float32)
+    for e in (-0.4, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3, 1.0):
+        sun = (math.radians(e), math.radians(37.0), ALPHA)
+        out = _run(h, g, sun, 2000.0)
+        sinp = oracle.sin_elev(h, g, R, sun[0], sun[1])
+        rho, dl = R + h0, 0.5 * g
+        c = (2 * rho * sinp + dl) / (np.sqrt(rho * rho + 2 * dl * rho * sinp + dl * dl) + rho)
+        d = np.clip(c * np.sqrt(1 - sinp ** 2) / ALPHA, -1, 1)
+        f = (np.pi - np.arccos(d) + d * np.sqrt(1 - d * d)) / np.pi
+        inner = np.zeros((ny, nx), bool)
+        inner[1:-1, 1:-1] = True
+        inner = inner.ravel()
+        assert np.all(out["argmin"][inner] == 1)
+        assert np.abs(out["light"][inner] - f[inner]).max() <= LIGHT_TOL
+
+
+# --------------------------------------------------------------- backward
+def _grad_case(n=96, k_sun=1):
+    inst = make_instance("diff", n=n)
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][k_sun]
+    alpha = math.radians(1.5)   # a wider disc puts more rays in the penumbra
+    return h, g, (elev, az, alpha), 3000.0
+
+
+@pytest.mark.parametrize("k_sun", [0, 1, 2, 3])
+def test_backward_vs_oracle_gradient(k_sun):
+    h, g, sun, lmax = _grad_case(k_sun=k_sun)
+    ht = _dev(h)
+    hf = ss.Heightfield(ht, g, R)
+    mip = ss.ss_build_maxmip(hf)
+    s = ss.Sun(*sun)
+    res = ss.ss_shadow_forward(hf, mip, s, lmax)
+    am_gpu = res["argmin"].cpu().numpy().astype(np.int64)
+    ol, oa, oc = oracle.shadow(h, g, R, sun[0], sun[1], sun[2], lmax)
+    gl = np.random.default_rng(3 + k_sun).normal(size=h.size)
+    gl[am_gpu != oa] = 0.0          # tie rays: the two argmins give different subgradients
+    gh_gpu, gs_gpu = ss.ss_shadow_backward(hf, s, lmax, res["argmin"],
+                                           torch.from_numpy(gl.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    gh_o, gs_o = oracle.grad(h, g, R, sun[0], sun[1], sun[2], oa,
+                             gl.astype(np.float32).astype(np.float64))
+    gh_gpu = gh_gpu.cpu().numpy().astype(np.float64)
+    scale = np.abs(gh_o).max()
+    assert scale > 0
+    assert np.abs(gh_gpu - gh_o).max() <= 1e-4 * scale
+    np.testing.assert_allclose(gs_gpu.cpu().numpy(), gs_o, rtol=1e-4, atol=1e-6 * np.abs(gs_o).max())
+
+
+def test_autograd_function_matches_oracle():
+    h, g, sun, lmax = _grad_case(n=80, k_sun=2)
+    target = torch.rand(h.size, device="cuda", dtype=torch.float32)
+    ht = _dev(h).requires_grad_(True)
+    ang = torch.tensor([sun[0], sun[1]], dtype=torch.float64, requires_grad=True)
+    light = ss.shadow(ht, ang, g, R, sun[2], lmax)
+    loss = ((light - target) ** 2).mean()
+    gh, gang = torch.autograd.grad(loss, [ht, ang])
+    ol, oa, oc = oracle.shadow(h, g, R, sun[0], sun[1], sun[2], lmax)
+    gl = 2.0 * (light.detach().cpu().numpy().astype(np.float64) - target.cpu().numpy()) / h.size
+    gh_o, gs_o = oracle.grad(h, g, R, sun[0], sun[1], sun[2], oa, gl)
+    assert np.abs(light.detach().cpu().numpy() - ol).max() <= LIGHT_TOL
+    scale = np.abs(gh_o).max()
+    assert np.abs(gh.cpu().numpy() - gh_o).max() <= 1e-4 * scale
+    np.testing.assert_allclose(gang.numpy(), gs_o[:2], rtol=1e-4, atol=1e-7)
