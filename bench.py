@@ -47,6 +47,8 @@ def parse_args(argv=None):
     p.add_argument("--leaf-level", type=int, default=-1)
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--size", type=int, default=0,
+                   help="profiling only: run the mid recipe at this tile size instead of 4096")
     return p.parse_args(argv)
 
 
@@ -137,10 +139,14 @@ def oracle_rate(inst, seconds, seed=2005):
         oracle.shadow(h, g, inst["radius"], elev, az, inst["alpha"], inst["lmax"], uv=uv)
         return time.perf_counter() - t0
 
-    n0 = 256
-    t0 = run(n0)
-    n = int(max(n0, min(4_000_000, n0 * seconds / max(t0, 1e-3))))
-    t = run(n)
+    # calibrate on growing samples until one takes >= 1/8 of the target
+    n, t = 1024, run(1024)
+    while t < seconds / 8 and n < 4_000_000:
+        n = int(min(4_000_000, n * max(2.0, min(16.0, seconds / 8 / max(t, 1e-4)))))
+        t = run(n)
+    if t < 0.8 * seconds:
+        n = int(min(4_000_000, n * seconds / t))
+        t = run(n)
     cores = oracle.num_threads()
     sample = (f"{n} seeded random rays of the {nx}x{ny} tile (every one of the "
               f"{int(inst['lmax'] / (0.5 * g))} samples per ray evaluated in FP64)")
@@ -164,7 +170,7 @@ def run_ours(args):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
 
-    inst = make_instance(CONFIG)
+    inst = make_instance(CONFIG, n=args.size or None)
     h_np = inst["h"]
     ny, nx = h_np.shape
     n_rays = nx * ny
