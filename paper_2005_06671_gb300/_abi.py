@@ -35,7 +35,8 @@ class SSSun(ctypes.Structure):
 
 class SSParams(ctypes.Structure):
     _fields_ = [("max_len_m", c_f64), ("step_texels", c_f64), ("flags", c_u32),
-                ("block_threads", c_i32), ("leaf_level", c_i32), ("reserved", c_i32)]
+                ("block_threads", c_i32), ("leaf_level", c_i32), ("rays_per_thread", c_i32),
+                ("refill_min", c_i32), ("reserved", c_i32)]
 
 
 class SSRays(ctypes.Structure):

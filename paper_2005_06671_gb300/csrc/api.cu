@@ -49,6 +49,8 @@ ss_status check_params(const ss_params* p, double g, int32_t* J, double* delta) 
         (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32 != 0))
         return SS_ERR_INVALID_ARG;
     if (p->leaf_level < -1 || p->leaf_level > 16) return SS_ERR_INVALID_ARG;
+    if (p->rays_per_thread < 0 || p->rays_per_thread > 4096) return SS_ERR_INVALID_ARG;
+    if (p->refill_min < 0 || p->refill_min > 32) return SS_ERR_INVALID_ARG;
     if (p->reserved != 0) return SS_ERR_INVALID_ARG;
     double st = p->step_texels == 0.0 ? 0.5 : p->step_texels;
     double d = st * g;
@@ -153,6 +155,8 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.kleaf = params->leaf_level < 0 ? 3 : params->leaf_level;
     a.flags = params->flags;
     int block = params->block_threads ? params->block_threads : 256;
+    a.rays_per_block = (int64_t)block * (params->rays_per_thread > 0 ? params->rays_per_thread : 8);
+    a.refill_min = params->refill_min > 0 ? params->refill_min : 8;
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);

@@ -1,9 +1,9 @@
 // Forward (exact max-mip descent and uniform stepping) and backward kernels.
 //
-// Work decomposition: one thread per shadow ray, rays taken in chunks of 32
-// consecutive ray ids per warp (grid mode: 32 neighbouring texels of a row,
-// whose samples at equal j touch neighbouring texels, so gathers coalesce),
-// chunks distributed grid-stride over a grid sized to the SM count.
+// Work decomposition: one thread walks one shadow ray at a time; each block
+// owns a contiguous range of ray ids (grid mode: row-major texels, so a warp's
+// rays are neighbours whose samples touch neighbouring texels) and its lanes
+// draw rays from that range as they finish (see refill()).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -59,120 +59,194 @@ __device__ __forceinline__ void setup_ray(const FwdArgs& a, int64_t r, float spa
     make_rayf(a.T, G, href, span, rf);
 }
 
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Scheduling shared by both forward kernels.  Block b owns rays
+// [b*rays_per_block, ...) (grid oversubscribes the SMs so the hardware block
+// scheduler balances them).  Each lane walks one ray; when at least
+// refill_min lanes of a warp are idle, those lanes take the next rays of the
+// block pool at once (ballot + one shared-memory atomic per warp), so lanes
+// whose rays finish early do not idle until the slowest lane is done.
+struct BlockPool {
+    int64_t lo;
+    int32_t cnt;
+};
+
+__device__ __forceinline__ BlockPool block_pool(const FwdArgs& a, int32_t* s_next) {
+    if (threadIdx.x == 0) *s_next = 0;
+    BlockPool P;
+    const int64_t n = ray_count(a.T, a.R);
+    P.lo = (int64_t)blockIdx.x * a.rays_per_block;
+    int64_t c = n - P.lo;
+    P.cnt = (int32_t)(c < a.rays_per_block ? c : a.rays_per_block);
+    return P;
+}
+
+// Returns the ray index this lane should start (or -1); updates `open`.
+__device__ __forceinline__ int64_t refill(const FwdArgs& a, const BlockPool& P, int32_t* s_next,
+                                          bool idle_lane, bool& open) {
+    const unsigned idle = __ballot_sync(kFull, idle_lane);
+    if (!open || idle == 0 || (idle != kFull && __popc(idle) < a.refill_min)) return -1;
+    const int nidle = __popc(idle);
+    int base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(s_next, nidle);
+    base = __shfl_sync(kFull, base, 0);
+    if (base + nidle >= P.cnt) open = false;
+    if (!idle_lane) return -1;
+    const int my = base + __popc(idle & lanemask_lt());
+    return my < P.cnt ? P.lo + my : -1;
+}
+
 // ---------------------------------------------------------------- descent
 // Stackless depth-first walk over aligned sample blocks [s0+1, s0+2^k]:
-// a block is bounded through the mip (node_bound) and skipped when its bound
-// exceeds the running minimum, else split; blocks of <= 2^kleaf samples are
+// a block's bound (probe) is compared with the running minimum; blocks that
+// cannot win are skipped, the others split; blocks of <= 2^kleaf samples are
 // evaluated sample by sample.  After a block, the walk continues at
-// s0 += 2^k with k = ctz(s0) -- the next block in near-to-far order.  Samples
-// are therefore evaluated in increasing j, and a strict '<' keeps the smallest
-// j among equal costs.
+// s0 += 2^k with k = ctz(s0), the next block in near-to-far order, so samples
+// are evaluated in increasing j and a strict '<' keeps the smallest j among
+// equal costs.  Each loop iteration is exactly one probe per active lane.
 template <bool kCount>
-__global__ void __launch_bounds__(256) dp_forward_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(256, 4) dp_forward_kernel(const FwdArgs a) {
     __shared__ const float* s_ptr[kMaxLevels];
     __shared__ int64_t s_pitch[kMaxLevels];
+    __shared__ int32_t s_next;
     if (threadIdx.x < kMaxLevels) {
         s_ptr[threadIdx.x] = a.P.ptr[threadIdx.x];
         s_pitch[threadIdx.x] = a.P.pitch[threadIdx.x];
     }
+    const BlockPool P = block_pool(a, &s_next);
     __syncthreads();
     const float span = a.stats[0] - a.stats[1];
-    const int64_t n = ray_count(a.T, a.R);
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int32_t kleaf = a.kleaf;
+    const int32_t kleaf = a.kleaf, levels = a.P.levels;
 
-    for (int64_t base = warp * 32; base < n; base += warps * 32) {
-        const int64_t r = base + lane;
-        if (r >= n) continue;
-        RayF rf;
-        setup_ray(a, r, span, rf);
-        float best = INFINITY;
-        int32_t bestj = -1, nb = 0, nl = 0;
-        const int32_t jlo = rf.j_lo, jhi = rf.j_hi;
-        if (jhi >= jlo) {
-            int32_t K = jhi <= 1 ? 0 : 32 - __clz(jhi - 1);   // 2^K >= jhi
-            int32_t s0 = 0;
-            int32_t k = K > kleaf ? K : 0;
-            while (true) {
-                bool advance = true;
-                if (k > 0) {
-                    int32_t ja = max(s0 + 1, jlo), jb = min(s0 + (1 << k), jhi);
-                    if (ja <= jb) {
-                        float lb = node_bound(a.T, a.P, s_ptr, s_pitch, rf, ja, jb);
-                        if (kCount) ++nb;
-                        if (!(lb > best)) {
-                            k = (k - 1 > kleaf) ? k - 1 : 0;
-                            advance = false;
-                        }
-                    }
-                } else {
-                    int32_t j = s0 + 1;
-                    if (j >= jlo) {
-                        float c = leaf_cost(a.T, rf, j);
-                        if (kCount) ++nl;
-                        if (c < best) {
-                            best = c;
-                            bestj = j;
-                        }
-                    }
+    int64_t r = -1;
+    RayF rf;
+    float best = INFINITY;
+    int32_t bestj = -1, nb = 0, nl = 0, s0 = 0, k = 0;
+    bool open = true;
+    while (true) {
+        const int64_t nr = refill(a, P, &s_next, r < 0, open);
+        if (nr >= 0) {
+            r = nr;
+            setup_ray(a, r, span, rf);
+            best = INFINITY;
+            bestj = -1;
+            nb = nl = s0 = 0;
+            const int32_t K = rf.j_hi <= 1 ? 0 : 32 - __clz(rf.j_hi - 1);   // 2^K >= j_hi
+            k = K > kleaf ? K : 0;
+            if (rf.j_hi < rf.j_lo) {   // no usable sample
+                finish_ray(a, r, rf, best, bestj, 0, 0);
+                r = -1;
+            }
+        }
+        if (__ballot_sync(kFull, r >= 0) == 0) {
+            if (!open) break;
+            continue;
+        }
+        if (r < 0) continue;
+        const bool leaf = (k == 0);
+        int32_t ja = leaf ? s0 + 1 : max(s0 + 1, rf.j_lo);
+        int32_t jb = leaf ? s0 + 1 : min(s0 + (1 << k), rf.j_hi);
+        const bool valid = leaf ? (ja >= rf.j_lo) : (ja <= jb);
+        if (!valid) ja = jb = rf.j_lo;   // keep the probe in range; result unused
+        const float v = probe(a.T, s_ptr, s_pitch, levels, rf, ja, jb, leaf);
+        bool advance = true;
+        if (valid) {
+            if (leaf) {
+                if (kCount) ++nl;
+                if (v < best) {
+                    best = v;
+                    bestj = ja;
                 }
-                if (advance) {
-                    s0 += 1 << k;
-                    if (s0 >= jhi) break;
-                    k = __ffs(s0) - 1;
-                    if (k <= kleaf) k = 0;
+            } else {
+                if (kCount) ++nb;
+                if (!(v > best)) {
+                    k = (k - 1 > kleaf) ? k - 1 : 0;
+                    advance = false;
                 }
             }
         }
-        finish_ray(a, r, rf, best, bestj, nb, nl);
+        if (advance) {
+            s0 += 1 << k;
+            if (s0 >= rf.j_hi) {
+                finish_ray(a, r, rf, best, bestj, nb, nl);
+                r = -1;
+            } else {
+                k = __ffs(s0) - 1;
+                if (k <= kleaf) k = 0;
+            }
+        }
     }
 }
 
 // ---------------------------------------------------------------- uniform
-// Every usable sample in order.  Early exit (exact): with H(t) = h_p + rise(t)
-// convex and H(0) = h_p <= max h, g(t) = (H(t) - max h - G)/t is
-// non-decreasing and bounds every later sample's cost from below; once
-// g(t_j) >= best no later sample can win.  G = 3 guards covers the float32
-// rounding of both sides.
+// Every usable sample in order, same scheduling as the descent.  Early exit
+// (exact): with H(t) = h_p + rise(t) convex and H(0) = h_p <= max h,
+// g(t) = (H(t) - max h - G)/t is non-decreasing and bounds every later
+// sample's cost from below; once g(t_j) >= best no later sample can win.
+// G = 3 guards covers the float32 rounding of both sides.
 template <bool kCount>
-__global__ void __launch_bounds__(256) uniform_forward_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(256, 4) uniform_forward_kernel(const FwdArgs a) {
+    __shared__ int32_t s_next;
+    const BlockPool P = block_pool(a, &s_next);
+    __syncthreads();
     const float hmax = a.stats[0];
     const float span = a.stats[0] - a.stats[1];
-    const int64_t n = ray_count(a.T, a.R);
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const bool allow_exit = !(a.flags & 0x2u);
 
-    for (int64_t base = warp * 32; base < n; base += warps * 32) {
-        const int64_t r = base + lane;
-        if (r >= n) continue;
-        RayF rf;
-        setup_ray(a, r, span, rf);
-        float best = INFINITY;
-        int32_t bestj = -1, nl = 0;
-        const float hmax_rel = hmax - rf.href;
-        const bool exit_ok = allow_exit && (rf.X <= hmax_rel);
-        const float tJ = (float)rf.j_hi * a.T.delta_f;
-        const float rb = fmaxf(rise_bound(rf, tJ), 0.25f * rf.B * rf.B * rf.inv_rho);
-        const float G = 3.0f * kGuardRel * (rf.guard0 + fabsf(hmax_rel) + rb);
-        for (int32_t j = rf.j_lo; j <= rf.j_hi; ++j) {
-            float rise;
-            float c = leaf_cost(a.T, rf, j, &rise);
-            if (kCount) ++nl;
-            if (c < best) {
-                best = c;
-                bestj = j;
-            }
-            if (exit_ok && (j & 3) == 0) {
-                float t = (float)j * a.T.delta_f;
-                float g = (((rf.X + rise) - hmax_rel) - G) / t;
-                if (g >= best) break;
+    int64_t r = -1;
+    RayF rf;
+    float best = INFINITY, hmax_rel = 0.0f, G = 0.0f;
+    int32_t bestj = -1, nl = 0, j = 0;
+    bool exit_ok = false, open = true;
+    while (true) {
+        const int64_t nr = refill(a, P, &s_next, r < 0, open);
+        if (nr >= 0) {
+            r = nr;
+            setup_ray(a, r, span, rf);
+            best = INFINITY;
+            bestj = -1;
+            nl = 0;
+            j = rf.j_lo;
+            hmax_rel = hmax - rf.href;
+            exit_ok = allow_exit && (rf.X <= hmax_rel);
+            const float tJ = (float)rf.j_hi * a.T.delta_f;
+            const float rb = fmaxf(rise_bound(rf, tJ), 0.25f * rf.B * rf.B * rf.inv_rho);
+            G = 3.0f * kGuardRel * (rf.guard0 + fabsf(hmax_rel) + rb);
+            if (rf.j_hi < rf.j_lo) {
+                finish_ray(a, r, rf, best, bestj, 0, 0);
+                r = -1;
             }
         }
-        finish_ray(a, r, rf, best, bestj, 0, nl);
+        if (__ballot_sync(kFull, r >= 0) == 0) {
+            if (!open) break;
+            continue;
+        }
+        if (r < 0) continue;
+        float rise;
+        const float c = leaf_cost(a.T, rf, j, &rise);
+        if (kCount) ++nl;
+        if (c < best) {
+            best = c;
+            bestj = j;
+        }
+        bool done = (j >= rf.j_hi);
+        if (!done && exit_ok && (j & 3) == 0) {
+            const float t = __fmul_rn((float)j, a.T.delta_f);
+            const float g = (((rf.X + rise) - hmax_rel) - G) / t;
+            done = (g >= best);
+        }
+        ++j;
+        if (done) {
+            finish_ray(a, r, rf, best, bestj, 0, nl);
+            r = -1;
+        }
     }
 }
 
@@ -293,21 +367,26 @@ static int resident_grid(K kernel, int block, int64_t n_threads) {
     return (int)(want < cap ? want : cap);
 }
 
-cudaError_t launch_dp_forward(const FwdArgs& a, int block, cudaStream_t s) {
+static int pool_grid(const FwdArgs& a) {
     int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
+    return (int)((n + a.rays_per_block - 1) / a.rays_per_block);
+}
+
+cudaError_t launch_dp_forward(const FwdArgs& a, int block, cudaStream_t s) {
+    const int grid = pool_grid(a);
     if (a.O.counters)
-        dp_forward_kernel<true><<<resident_grid(dp_forward_kernel<true>, block, n), block, 0, s>>>(a);
+        dp_forward_kernel<true><<<grid, block, 0, s>>>(a);
     else
-        dp_forward_kernel<false><<<resident_grid(dp_forward_kernel<false>, block, n), block, 0, s>>>(a);
+        dp_forward_kernel<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_uniform_forward(const FwdArgs& a, int block, cudaStream_t s) {
-    int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
+    const int grid = pool_grid(a);
     if (a.O.counters)
-        uniform_forward_kernel<true><<<resident_grid(uniform_forward_kernel<true>, block, n), block, 0, s>>>(a);
+        uniform_forward_kernel<true><<<grid, block, 0, s>>>(a);
     else
-        uniform_forward_kernel<false><<<resident_grid(uniform_forward_kernel<false>, block, n), block, 0, s>>>(a);
+        uniform_forward_kernel<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

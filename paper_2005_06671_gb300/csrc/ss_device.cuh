@@ -227,39 +227,43 @@ __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double
 }
 
 // ------------------------------------------------------------ float32 leaf
+// Every operation that produces a sample value is an explicitly rounded
+// intrinsic (__fadd_rn, __fmul_rn, __fmaf_rn, __fdiv_rn, __fsqrt_rn), which the
+// compiler never contracts or reorders: the value is the same bits in every
+// kernel and inlining context that evaluates it.
 struct Pos {
     int32_t i;
     float f;
 };
 
+__device__ __forceinline__ float corr_of(const RayF& r, float jf) {
+    float jb = __fmul_rn(jf, r.b);
+    return __fdividef(__fmul_rn(jf, jb), __fadd_rn(1.0f, jb));   // j - j/(1 + b j)
+}
+
 // Texel coordinate of sample j along one axis: integer part exact, fraction
-// accurate to ~1e-7 texel.  Base clamped to [0, n-2] (fraction absorbs it).
+// accurate to ~1e-7 texel.  Base clamped to [0, n-2] (the fraction absorbs it).
 __device__ __forceinline__ Pos axis_pos(int32_t i0, float f0, float a_hi, float a_lo, float a,
                                         float corr, float jf, int32_t n) {
-    float p = jf * a_hi;                 // exact
+    float p = __fmul_rn(jf, a_hi);       // exact: a_hi has <= 8 significant bits
     float kp = floorf(p);
-    float fp = p - kp;                   // exact
-    float s = f0 + fp + fmaf(jf, a_lo, -a * corr);
+    float fp = __fsub_rn(p, kp);         // exact
+    float s = __fadd_rn(__fadd_rn(f0, fp), __fmaf_rn(jf, a_lo, -__fmul_rn(a, corr)));
     float fs = floorf(s);
     int32_t i = i0 + (int32_t)kp + (int32_t)fs;
-    float f = s - fs;
+    float f = __fsub_rn(s, fs);
     int32_t ic = min(max(i, 0), n - 2);
-    f += (float)(i - ic);
+    f = __fadd_rn(f, (float)(i - ic));
     Pos P;
     P.i = ic;
     P.f = f;
     return P;
 }
 
-__device__ __forceinline__ float corr_of(const RayF& r, float jf) {
-    float jb = jf * r.b;
-    return __fdividef(jf * jb, 1.0f + jb);   // j - j/(1 + b j)
-}
-
 // |p + t s| - |p| without cancellation.
 __device__ __forceinline__ float rise_of(const RayF& r, float t) {
-    float w = t * (r.B + t);
-    return w / (r.rho + sqrtf(fmaf(r.rho, r.rho, w)));
+    float w = __fmul_rn(t, __fadd_rn(r.B, t));
+    return __fdiv_rn(w, __fadd_rn(r.rho, __fsqrt_rn(__fmaf_rn(r.rho, r.rho, w))));
 }
 
 // upper bound of |rise(t)| without a square root
@@ -267,45 +271,53 @@ __device__ __forceinline__ float rise_bound(const RayF& r, float t) {
     return fabsf(t * (r.B + t)) * r.inv_rho;
 }
 
-__device__ __forceinline__ float bilinear_rel(const float* __restrict__ h, int64_t pitch,
-                                              const Pos& pu, const Pos& pv, float href) {
-    const float* p = h + (int64_t)pv.i * pitch + pu.i;
-    float d00 = __ldg(p) - href, d10 = __ldg(p + 1) - href;
-    float d01 = __ldg(p + pitch) - href, d11 = __ldg(p + pitch + 1) - href;
-    float top = fmaf(pu.f, d10 - d00, d00);
-    float bot = fmaf(pu.f, d11 - d01, d01);
-    return fmaf(pv.f, bot - top, top);
+__device__ __forceinline__ float bilerp_rn(float d00, float d10, float d01, float d11, float fu,
+                                           float fv) {
+    float top = __fmaf_rn(fu, __fsub_rn(d10, d00), d00);
+    float bot = __fmaf_rn(fu, __fsub_rn(d11, d01), d01);
+    return __fmaf_rn(fv, __fsub_rn(bot, top), top);
 }
 
-// Cost of sample j (float32); identical in every kernel.
+// Cost of sample j (float32); the uniform kernel's sample value.  probe() with
+// ja == jb returns the same bits.
 __device__ __forceinline__ float leaf_cost(const Tile& T, const RayF& r, int32_t j,
                                            float* rise_out = nullptr) {
     float jf = (float)j;
     float corr = corr_of(r, jf);
     Pos pu = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, corr, jf, T.nx);
     Pos pv = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, corr, jf, T.ny);
-    float t = jf * T.delta_f;
+    float t = __fmul_rn(jf, T.delta_f);
     float rise = rise_of(r, t);
     if (rise_out) *rise_out = rise;
-    float hb = bilinear_rel(T.h, T.pitch, pu, pv, r.href);
-    return ((r.X + rise) - hb) / t;
+    const float* p = T.h + (int64_t)pv.i * T.pitch + pu.i;
+    float d00 = __fsub_rn(__ldg(p), r.href), d10 = __fsub_rn(__ldg(p + 1), r.href);
+    float d01 = __fsub_rn(__ldg(p + T.pitch), r.href);
+    float d11 = __fsub_rn(__ldg(p + T.pitch + 1), r.href);
+    float hb = bilerp_rn(d00, d10, d01, d11, pu.f, pv.f);
+    return __fdiv_rn(__fsub_rn(__fadd_rn(r.X, rise), hb), t);
 }
 
-// Lower bound of every leaf_cost(j), ja <= j <= jb, through the maximum mipmap:
-// M = max of the heights under the footprint box of the samples (Eq. optimumk2:
-// the clearance over an interval is at least the ray's lowest height minus
-// the maximum terrain height below it).  guard = 2^-19 (|X| + |rise| + |M -
-// h_ref| + span) covers every float32 rounding of leaf_cost and of this bound.
-__device__ __forceinline__ float node_bound(const Tile& T, const Pyramid& P,
-                                            const float* const* lev_ptr,
-                                            const int64_t* lev_pitch, const RayF& r,
-                                            int32_t ja, int32_t jb) {
+// One probe of the descent, a single code path for both kinds so that a warp
+// whose lanes mix them stays converged:
+//  * leaf (ja == jb): the cost of sample ja, bit-identical to leaf_cost();
+//  * block [ja, jb]: a lower bound of every leaf cost in it, through the
+//    maximum mipmap (Eq. optimumk2: the clearance over an interval is at least
+//    the ray's lowest height there minus the maximum terrain height below it).
+//    M = max over the 2x2 cells, at the coarsest level whose cells cover the
+//    texel footprint box of the block's samples; the guard
+//    2^-19 (|X| + |rise| + |M - h_ref| + span) covers every float32 rounding of
+//    the leaf and of the bound, so no sample that could win is skipped.
+__device__ __forceinline__ float probe(const Tile& T, const float* const* lev_ptr,
+                                       const int64_t* lev_pitch, int32_t levels, const RayF& r,
+                                       int32_t ja, int32_t jb, bool leaf) {
     float fa = (float)ja, fb = (float)jb;
     float ca = corr_of(r, fa), cb = corr_of(r, fb);
     Pos ua = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, ca, fa, T.nx);
-    Pos ub = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, cb, fb, T.nx);
     Pos va = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, ca, fa, T.ny);
+    Pos ub = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, cb, fb, T.nx);
     Pos vb = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, cb, fb, T.ny);
+    float ta = __fmul_rn(fa, T.delta_f), tb = __fmul_rn(fb, T.delta_f);
+    // footprint box of the block (all samples lie between the two ends)
     int32_t xa0 = ua.i - (ua.f < kPosEps ? 1 : 0), xb0 = ub.i - (ub.f < kPosEps ? 1 : 0);
     int32_t xa1 = ua.i + (ua.f + kPosEps >= 1.0f ? 2 : 1), xb1 = ub.i + (ub.f + kPosEps >= 1.0f ? 2 : 1);
     int32_t ya0 = va.i - (va.f < kPosEps ? 1 : 0), yb0 = vb.i - (vb.f < kPosEps ? 1 : 0);
@@ -315,19 +327,29 @@ __device__ __forceinline__ float node_bound(const Tile& T, const Pyramid& P,
     int32_t e = max(x1 - x0, y1 - y0);
     int32_t m = e <= 1 ? 0 : 31 - __clz(e);
     if (((x1 >> m) - (x0 >> m)) > 1 || ((y1 >> m) - (y0 >> m)) > 1) ++m;
-    m = min(m, P.levels - 1);
+    m = min(m, levels - 1);
+    if (leaf) {   // the sample's own bilinear cell at level 0
+        x0 = ua.i; x1 = ua.i + 1; y0 = va.i; y1 = va.i + 1; m = 0;
+    }
     const float* lp = lev_ptr[m];
     int64_t pm = lev_pitch[m];
     int32_t xa = x0 >> m, xb = x1 >> m, ya = y0 >> m, yb = y1 >> m;
-    float M = fmaxf(fmaxf(__ldg(lp + (int64_t)ya * pm + xa), __ldg(lp + (int64_t)ya * pm + xb)),
-                    fmaxf(__ldg(lp + (int64_t)yb * pm + xa), __ldg(lp + (int64_t)yb * pm + xb)));
-    float Mrel = M - r.href;
-    float ta = fa * T.delta_f, tb = fb * T.delta_f;
-    float tmin = (r.tv > ta) ? fminf(r.tv, tb) : ta;
-    float rmin = rise_of(r, tmin);
-    float guard = kGuardRel * (r.guard0 + fabsf(Mrel) + rise_bound(r, tb) + fabsf(rmin));
-    float num = ((r.X + rmin) - Mrel) - guard;
-    return num / (num >= 0.0f ? tb : ta);
+    float d00 = __fsub_rn(__ldg(lp + (int64_t)ya * pm + xa), r.href);
+    float d10 = __fsub_rn(__ldg(lp + (int64_t)ya * pm + xb), r.href);
+    float d01 = __fsub_rn(__ldg(lp + (int64_t)yb * pm + xa), r.href);
+    float d11 = __fsub_rn(__ldg(lp + (int64_t)yb * pm + xb), r.href);
+    float tstar = (leaf || !(r.tv > ta)) ? ta : fminf(r.tv, tb);
+    float rise = rise_of(r, tstar);
+    float V = leaf ? bilerp_rn(d00, d10, d01, d11, ua.f, va.f)
+                   : fmaxf(fmaxf(d00, d10), fmaxf(d01, d11));
+    float num = __fsub_rn(__fadd_rn(r.X, rise), V);
+    float guard = kGuardRel * (r.guard0 + fabsf(V) + rise_bound(r, tb) + fabsf(rise));
+    float den = ta;
+    if (!leaf) {
+        num = __fsub_rn(num, guard);
+        den = num >= 0.0f ? tb : ta;
+    }
+    return __fdiv_rn(num, den);
 }
 
 // ------------------------------------------------------ FP64 re-evaluation

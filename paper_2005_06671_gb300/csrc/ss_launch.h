@@ -29,6 +29,8 @@ struct FwdArgs {
     const float* stats;   // device: (global max, global min) of the heights
     int32_t kleaf;
     uint32_t flags;
+    int64_t rays_per_block;   // rays owned by one block
+    int32_t refill_min;       // idle lanes that trigger a warp refill
 };
 
 struct BwdArgs {

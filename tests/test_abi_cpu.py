@@ -42,7 +42,7 @@ def test_status_strings_and_layout_queries():
 def _good():
     hf = SSHeightfield(FAKE, 64, 64, 64, 10.0, 1737.4e3, 0)
     sun = SSSun(math.radians(1.0), 0.5, math.radians(0.2665))
-    prm = SSParams(1000.0, 0.5, 0, 0, -1, 0)
+    prm = SSParams(1000.0, 0.5, 0, 0, -1, 0, 0, 0)
     rays = SSRays(0, 0, None, None)
     out = SSOutputs(FAKE, FAKE, None, None)
     return hf, sun, prm, rays, out
@@ -75,6 +75,9 @@ def _fwd(hf, sun, prm, rays, out, mip=FAKE):
     (lambda a: setattr(a[2], "block_threads", 100), 1),
     (lambda a: setattr(a[2], "leaf_level", 40), 1),
     (lambda a: setattr(a[2], "reserved", 1), 1),
+    (lambda a: setattr(a[2], "rays_per_thread", -1), 1),
+    (lambda a: setattr(a[2], "rays_per_thread", 5000), 1),
+    (lambda a: setattr(a[2], "refill_min", 33), 1),
     (lambda a: setattr(a[3], "mode", 7), 1),
     (lambda a: (setattr(a[3], "mode", 1), setattr(a[3], "n", -3)), 2),
     (lambda a: (setattr(a[3], "mode", 1), setattr(a[3], "n", 5)), 1),
