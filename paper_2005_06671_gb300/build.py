@@ -15,7 +15,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+OUT = os.environ.get("SS_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsoftshadow.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -47,7 +47,9 @@ def up_to_date():
 
 
 def build(force=False, verbose=False, extra_flags=()):
-    """Build the library; returns its path."""
+    """Build the library; returns its path.  SS_NVCC_FLAGS (environment) adds
+    compiler flags, e.g. a -D tuning macro, for an alternate SS_BUILD_DIR."""
+    extra_flags = list(extra_flags) + os.environ.get("SS_NVCC_FLAGS", "").split()
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT, exist_ok=True)

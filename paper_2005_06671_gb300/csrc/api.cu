@@ -104,6 +104,7 @@ ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, doubl
     T.inv_gR = 1.0 / (hf->texel_m * hf->radius_m);
     T.alpha = sun->angular_radius_rad;
     T.delta_f = (float)delta;
+    T.inv_delta_f = (float)(1.0 / delta);
     T.alpha_f = (float)sun->angular_radius_rad;
     return T;
 }

@@ -67,6 +67,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Minimum resident 256-thread blocks per SM for the forward kernels (caps
+// registers at 65536 / (256 * SS_FWD_MIN_BLOCKS)).
+#ifndef SS_FWD_MIN_BLOCKS
+#define SS_FWD_MIN_BLOCKS 4
+#endif
+
 // Scheduling shared by both forward kernels.  Block b owns rays
 // [b*rays_per_block, ...) (grid oversubscribes the SMs so the hardware block
 // scheduler balances them).  Each lane walks one ray; when at least
@@ -112,7 +118,7 @@ __device__ __forceinline__ int64_t refill(const FwdArgs& a, const BlockPool& P, 
 // are evaluated in increasing j and a strict '<' keeps the smallest j among
 // equal costs.  Each loop iteration is exactly one probe per active lane.
 template <bool kCount>
-__global__ void __launch_bounds__(256, 4) dp_forward_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(const FwdArgs a) {
     __shared__ const float* s_ptr[kMaxLevels];
     __shared__ int64_t s_pitch[kMaxLevels];
     __shared__ int32_t s_next;
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(256, 4) dp_forward_kernel(const FwdArgs a) {
 // sample's cost from below; once g(t_j) >= best no later sample can win.
 // G = 3 guards covers the float32 rounding of both sides.
 template <bool kCount>
-__global__ void __launch_bounds__(256, 4) uniform_forward_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel(const FwdArgs a) {
     __shared__ int32_t s_next;
     const BlockPool P = block_pool(a, &s_next);
     __syncthreads();

@@ -47,6 +47,7 @@ struct Tile {
     double inv_gR;             // 1 / (g R)
     double alpha;              // sun angular radius
     float delta_f;             // (float)delta
+    float inv_delta_f;         // (float)(1/delta)
     float alpha_f;
 };
 
@@ -80,17 +81,22 @@ struct Geom64 {
 struct RayF {
     int32_t iu0, iv0;          // integer part of the origin position
     float fu0, fv0;            // fractional part
+    float u0, v0;              // origin position (float) for block footprints
     float au_hi, au_lo, av_hi, av_lo;  // per-sample slope split so that j*a_hi is exact
     float au, av;              // (float) slopes
     float b;                   // projective coefficient
     float B;                   // 2 rho sin_e
-    float rho, rho2, inv_rho;
+    float rho;                 // R + h_p
+    float inv_2rho, inv_rho2;  // 1/(2 rho), 1/rho^2
+    float inv_rho;
     float X;                   // h_p - h_ref
     float href;
     float tv;                  // distance of the lowest ray point (sin_e < 0), else -1
     float guard0;              // |X| + height span of the tile
+    float pos_eps;             // footprint margin covering float32 block-end positions
     float cos_e;
     int32_t j_lo, j_hi;        // usable sample range (empty when j_lo > j_hi)
+    int32_t exact_rise;        // 1: the rise series may not converge fast enough
 };
 
 // ------------------------------------------------------------------ helpers
@@ -209,21 +215,34 @@ __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double
     r.iv0 = (int32_t)iv;
     r.fu0 = (float)(G.up - iu);
     r.fv0 = (float)(G.vp - iv);
+    r.u0 = (float)G.up;
+    r.v0 = (float)G.vp;
     split8(G.Au, r.au_hi, r.au_lo);
     split8(G.Av, r.av_hi, r.av_lo);
     r.au = (float)G.Au;
     r.av = (float)G.Av;
     r.b = (float)G.b;
-    r.B = (float)(2.0 * G.rho * G.sin_e);
+    double B = 2.0 * G.rho * G.sin_e;
+    r.B = (float)B;
     r.rho = (float)G.rho;
-    r.rho2 = (float)(G.rho * G.rho);
-    r.inv_rho = (float)(1.0 / G.rho);
+    r.inv_2rho = (float)(0.5 / G.rho);
+    r.inv_rho2 = (float)(1.0 / (G.rho * G.rho));
+    r.inv_rho = 2.0f * r.inv_2rho;
     r.X = (float)(G.hp - href);
     r.href = (float)href;
     r.tv = G.sin_e < 0.0 ? (float)(-G.rho * G.sin_e) : -1.0f;
     r.guard0 = fabsf(r.X) + span;
     r.cos_e = (float)G.cos_e;
     sample_range(T, G, r.j_lo, r.j_hi);
+    // |x| = |t (B + t)| / rho^2 over the ray; the 5-term series of the rise is
+    // used when |x| <= 1/32 (truncation < 1e-9 relative)
+    double tJ = (double)max(r.j_hi, 1) * T.delta;
+    double wmax = fmax(fabs(tJ * (B + tJ)), 0.25 * B * B);
+    r.exact_rise = (wmax / (G.rho * G.rho) > 0.03125) ? 1 : 0;
+    // float32 block-end positions u0 + a*tau err by <= ulp(coordinate) plus
+    // ~3 ulp of a*tau; the margin takes 4x that, plus 1e-3 texel
+    float amax = fmaxf(fabsf(r.au), fabsf(r.av));
+    r.pos_eps = 1e-3f + 5e-7f * (float)(T.nx + T.ny) + 8e-7f * amax * (float)max(r.j_hi, 1);
 }
 
 // ------------------------------------------------------------ float32 leaf
@@ -260,10 +279,26 @@ __device__ __forceinline__ Pos axis_pos(int32_t i0, float f0, float a_hi, float 
     return P;
 }
 
-// |p + t s| - |p| without cancellation.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// rise(t) = |p + t s| - |p| = w / (rho + sqrt(rho^2 + w)), w = t (2 rho sin_e + t),
+// without cancellation.  With x = w / rho^2 this is (w / 2 rho) * 2/(1 + sqrt(1 + x))
+// = (w / 2 rho) (1 - x/4 + x^2/8 - 5x^3/64 + 7x^4/128 - ...); for |x| <= 1/32 the
+// truncation error is < 1e-9 relative, else the closed form is used.
 __device__ __forceinline__ float rise_of(const RayF& r, float t) {
     float w = __fmul_rn(t, __fadd_rn(r.B, t));
-    return __fdiv_rn(w, __fadd_rn(r.rho, __fsqrt_rn(__fmaf_rn(r.rho, r.rho, w))));
+    if (r.exact_rise)
+        return __fdiv_rn(w, __fadd_rn(r.rho, __fsqrt_rn(__fmaf_rn(r.rho, r.rho, w))));
+    float x = __fmul_rn(w, r.inv_rho2);
+    float p = __fmaf_rn(x, 0.0546875f, -0.078125f);
+    p = __fmaf_rn(x, p, 0.125f);
+    p = __fmaf_rn(x, p, -0.25f);
+    p = __fmaf_rn(x, p, 1.0f);
+    return __fmul_rn(__fmul_rn(w, r.inv_2rho), p);
 }
 
 // upper bound of |rise(t)| without a square root
@@ -278,8 +313,18 @@ __device__ __forceinline__ float bilerp_rn(float d00, float d10, float d01, floa
     return __fmaf_rn(fv, __fsub_rn(bot, top), top);
 }
 
+// 1/t_j: delta^-1 times the hardware reciprocal of j (deterministic, <= 2 ulp)
+__device__ __forceinline__ float inv_t(const Tile& T, float jf) {
+    return __fmul_rn(T.inv_delta_f, rcp_approx(jf));
+}
+
+__device__ __forceinline__ const float* cell_ptr(const float* base, int64_t pitch, int32_t x,
+                                                 int32_t y) {
+    return base + ((int64_t)y * pitch + x);
+}
+
 // Cost of sample j (float32); the uniform kernel's sample value.  probe() with
-// ja == jb returns the same bits.
+// leaf == true returns the same bits.
 __device__ __forceinline__ float leaf_cost(const Tile& T, const RayF& r, int32_t j,
                                            float* rise_out = nullptr) {
     float jf = (float)j;
@@ -289,67 +334,76 @@ __device__ __forceinline__ float leaf_cost(const Tile& T, const RayF& r, int32_t
     float t = __fmul_rn(jf, T.delta_f);
     float rise = rise_of(r, t);
     if (rise_out) *rise_out = rise;
-    const float* p = T.h + (int64_t)pv.i * T.pitch + pu.i;
+    const float* p = cell_ptr(T.h, T.pitch, pu.i, pv.i);
     float d00 = __fsub_rn(__ldg(p), r.href), d10 = __fsub_rn(__ldg(p + 1), r.href);
     float d01 = __fsub_rn(__ldg(p + T.pitch), r.href);
     float d11 = __fsub_rn(__ldg(p + T.pitch + 1), r.href);
     float hb = bilerp_rn(d00, d10, d01, d11, pu.f, pv.f);
-    return __fdiv_rn(__fsub_rn(__fadd_rn(r.X, rise), hb), t);
+    return __fmul_rn(__fsub_rn(__fadd_rn(r.X, rise), hb), inv_t(T, jf));
+}
+
+// float32 texel position of sample j for block footprints (error <= pos_eps)
+__device__ __forceinline__ void block_end(const RayF& r, float jf, float& u, float& v) {
+    float tau = __fdividef(jf, __fmaf_rn(jf, r.b, 1.0f));
+    u = __fmaf_rn(r.au, tau, r.u0);
+    v = __fmaf_rn(r.av, tau, r.v0);
 }
 
 // One probe of the descent, a single code path for both kinds so that a warp
 // whose lanes mix them stays converged:
-//  * leaf (ja == jb): the cost of sample ja, bit-identical to leaf_cost();
+//  * leaf: the cost of sample ja, bit-identical to leaf_cost();
 //  * block [ja, jb]: a lower bound of every leaf cost in it, through the
 //    maximum mipmap (Eq. optimumk2: the clearance over an interval is at least
 //    the ray's lowest height there minus the maximum terrain height below it).
 //    M = max over the 2x2 cells, at the coarsest level whose cells cover the
-//    texel footprint box of the block's samples; the guard
-//    2^-19 (|X| + |rise| + |M - h_ref| + span) covers every float32 rounding of
-//    the leaf and of the bound, so no sample that could win is skipped.
+//    texel footprint box of the block's samples (the float32 end positions
+//    widened by pos_eps); the guard 2^-19 (|X| + |rise| + |M - h_ref| + span)
+//    covers every float32 rounding of the leaf and of the bound, so no sample
+//    that could win is skipped.
 __device__ __forceinline__ float probe(const Tile& T, const float* const* lev_ptr,
                                        const int64_t* lev_pitch, int32_t levels, const RayF& r,
                                        int32_t ja, int32_t jb, bool leaf) {
-    float fa = (float)ja, fb = (float)jb;
-    float ca = corr_of(r, fa), cb = corr_of(r, fb);
-    Pos ua = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, ca, fa, T.nx);
-    Pos va = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, ca, fa, T.ny);
-    Pos ub = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, cb, fb, T.nx);
-    Pos vb = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, cb, fb, T.ny);
-    float ta = __fmul_rn(fa, T.delta_f), tb = __fmul_rn(fb, T.delta_f);
-    // footprint box of the block (all samples lie between the two ends)
-    int32_t xa0 = ua.i - (ua.f < kPosEps ? 1 : 0), xb0 = ub.i - (ub.f < kPosEps ? 1 : 0);
-    int32_t xa1 = ua.i + (ua.f + kPosEps >= 1.0f ? 2 : 1), xb1 = ub.i + (ub.f + kPosEps >= 1.0f ? 2 : 1);
-    int32_t ya0 = va.i - (va.f < kPosEps ? 1 : 0), yb0 = vb.i - (vb.f < kPosEps ? 1 : 0);
-    int32_t ya1 = va.i + (va.f + kPosEps >= 1.0f ? 2 : 1), yb1 = vb.i + (vb.f + kPosEps >= 1.0f ? 2 : 1);
-    int32_t x0 = max(min(xa0, xb0), 0), x1 = min(max(xa1, xb1), T.nx - 1);
-    int32_t y0 = max(min(ya0, yb0), 0), y1 = min(max(ya1, yb1), T.ny - 1);
-    int32_t e = max(x1 - x0, y1 - y0);
-    int32_t m = e <= 1 ? 0 : 31 - __clz(e);
+    const float fa = (float)ja, fb = (float)jb;
+    // leaf position (the sample's bilinear cell)
+    const float ca = corr_of(r, fa);
+    const Pos ua = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, ca, fa, T.nx);
+    const Pos va = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, ca, fa, T.ny);
+    // block footprint box from both ends
+    float xa, ya, xb, yb;
+    block_end(r, fa, xa, ya);
+    block_end(r, fb, xb, yb);
+    const float e = r.pos_eps;
+    int32_t x0 = max((int32_t)floorf(fminf(xa, xb) - e), 0);
+    int32_t x1 = min((int32_t)floorf(fmaxf(xa, xb) + e) + 1, T.nx - 1);
+    int32_t y0 = max((int32_t)floorf(fminf(ya, yb) - e), 0);
+    int32_t y1 = min((int32_t)floorf(fmaxf(ya, yb) + e) + 1, T.ny - 1);
+    const int32_t ext = max(x1 - x0, y1 - y0);
+    int32_t m = ext <= 1 ? 0 : 31 - __clz(ext);
     if (((x1 >> m) - (x0 >> m)) > 1 || ((y1 >> m) - (y0 >> m)) > 1) ++m;
     m = min(m, levels - 1);
-    if (leaf) {   // the sample's own bilinear cell at level 0
+    if (leaf) {
         x0 = ua.i; x1 = ua.i + 1; y0 = va.i; y1 = va.i + 1; m = 0;
     }
-    const float* lp = lev_ptr[m];
-    int64_t pm = lev_pitch[m];
-    int32_t xa = x0 >> m, xb = x1 >> m, ya = y0 >> m, yb = y1 >> m;
-    float d00 = __fsub_rn(__ldg(lp + (int64_t)ya * pm + xa), r.href);
-    float d10 = __fsub_rn(__ldg(lp + (int64_t)ya * pm + xb), r.href);
-    float d01 = __fsub_rn(__ldg(lp + (int64_t)yb * pm + xa), r.href);
-    float d11 = __fsub_rn(__ldg(lp + (int64_t)yb * pm + xb), r.href);
-    float tstar = (leaf || !(r.tv > ta)) ? ta : fminf(r.tv, tb);
-    float rise = rise_of(r, tstar);
-    float V = leaf ? bilerp_rn(d00, d10, d01, d11, ua.f, va.f)
-                   : fmaxf(fmaxf(d00, d10), fmaxf(d01, d11));
+    const int64_t pm = lev_pitch[m];
+    const float* p = cell_ptr(lev_ptr[m], pm, x0 >> m, y0 >> m);
+    const int32_t dx = (x1 >> m) - (x0 >> m);
+    const int64_t dy = ((y1 >> m) - (y0 >> m)) * pm;
+    const float d00 = __fsub_rn(__ldg(p), r.href);
+    const float d10 = __fsub_rn(__ldg(p + dx), r.href);
+    const float d01 = __fsub_rn(__ldg(p + dy), r.href);
+    const float d11 = __fsub_rn(__ldg(p + dy + dx), r.href);
+    const float ta = __fmul_rn(fa, T.delta_f), tb = __fmul_rn(fb, T.delta_f);
+    const float tstar = (leaf || !(r.tv > ta)) ? ta : fminf(r.tv, tb);
+    const float rise = rise_of(r, tstar);
+    const float V = leaf ? bilerp_rn(d00, d10, d01, d11, ua.f, va.f)
+                         : fmaxf(fmaxf(d00, d10), fmaxf(d01, d11));
     float num = __fsub_rn(__fadd_rn(r.X, rise), V);
-    float guard = kGuardRel * (r.guard0 + fabsf(V) + rise_bound(r, tb) + fabsf(rise));
-    float den = ta;
+    float den_j = fa;
     if (!leaf) {
-        num = __fsub_rn(num, guard);
-        den = num >= 0.0f ? tb : ta;
+        num = __fsub_rn(num, kGuardRel * (r.guard0 + fabsf(V) + rise_bound(r, tb) + fabsf(rise)));
+        den_j = num >= 0.0f ? fb : fa;
     }
-    return __fdiv_rn(num, den);
+    return __fmul_rn(num, inv_t(T, den_j));
 }
 
 // ------------------------------------------------------ FP64 re-evaluation
