@@ -245,6 +245,10 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
+    # events for the untimed extra legs (independent of --steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+
     # ---- roofline of the descent kernel: gathered bytes from counted probes
     res = ss.ss_shadow_forward(hf, mip, sun, lmax, count_samples=True, want_cost=False,
                                leaf_level=args.leaf_level, block_threads=args.block)

@@ -104,10 +104,10 @@ typedef struct {
     int32_t block_threads; /* threads per block, multiple of 32 in [32, 256];
                               0 = 256                                          */
     int32_t leaf_level;    /* forward: subtrees of <= 2^leaf_level samples are
-                              evaluated sample by sample; -1 = default (3)     */
+                              evaluated sample by sample; -1 = default (2)     */
     int32_t rays_per_thread; /* forward kernels: a block owns block_threads x
                               rays_per_thread consecutive rays, in [0, 4096];
-                              0 = default (8)                                  */
+                              0 = default (16)                                 */
     int32_t refill_min;    /* forward kernels: a warp's idle lanes take new
                               rays once at least this many are idle, in
                               [0, 32]; 0 = default (8)                         */

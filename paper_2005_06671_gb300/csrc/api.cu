@@ -25,6 +25,7 @@ ss_status check_tile(const ss_heightfield* hf, int32_t min_dim) {
     if (hf->nx < min_dim || hf->ny < min_dim || hf->nx > SS_MAX_DIM || hf->ny > SS_MAX_DIM)
         return SS_ERR_BAD_SIZE;
     if (hf->pitch < hf->nx) return SS_ERR_BAD_SIZE;
+    if ((double)hf->pitch * (double)hf->ny > 4294967295.0) return SS_ERR_BAD_SIZE;
     if (!finite_pos(hf->texel_m) || !finite_pos(hf->radius_m)) return SS_ERR_INVALID_ARG;
     if (hf->projection != SS_PROJ_GNOMONIC && hf->projection != SS_PROJ_POLAR_STEREO)
         return SS_ERR_INVALID_ARG;
@@ -121,6 +122,22 @@ ss::Pyramid make_pyramid(const ss_heightfield* hf, const float* mip, const ss::M
     return P;
 }
 
+// The float32 ray rise uses a 5-term series in x = t (2 rho sin e + t) / rho^2
+// when |x| <= 1/32 holds for every ray of the launch.  Bound: |sin e| <=
+// |s_z| + sin(theta) |s_xy| with theta the angle from the tile centre to its
+// corner (x3 for listed origins, which may lie off the tile), and rho >= R/2
+// (heights above -R/2); then |x| <= t (4 |sin e| / R + 4 t / R^2).
+bool rise_series_ok(const ss_heightfield* hf, const ss_sun* sun, double tmax, int32_t mode) {
+    const double hx = 0.5 * (hf->nx - 1) * hf->texel_m, hy = 0.5 * (hf->ny - 1) * hf->texel_m;
+    double st = sqrt(hx * hx + hy * hy) / hf->radius_m;
+    if (mode != SS_RAYS_GRID) st *= 3.0;
+    st = fmin(st, 1.0);
+    const double sz = fabs(sin(sun->elevation_rad)), sxy = fabs(cos(sun->elevation_rad));
+    const double se = fmin(1.0, sz + st * sxy);
+    const double R = hf->radius_m;
+    return tmax * (4.0 * se / R + 4.0 * tmax / (R * R)) <= 0.03125;
+}
+
 enum class FwdKind { Descent, Uniform };
 
 ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip,
@@ -153,11 +170,12 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.O.cost = out->cost;
     a.O.counters = (params->flags & SS_FLAG_COUNT_SAMPLES) ? out->counters : nullptr;
     a.stats = mip + L.stats_offset;
-    a.kleaf = params->leaf_level < 0 ? 3 : params->leaf_level;
+    a.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
     a.flags = params->flags;
     int block = params->block_threads ? params->block_threads : 256;
-    a.rays_per_block = (int64_t)block * (params->rays_per_thread > 0 ? params->rays_per_thread : 8);
+    a.rays_per_block = (int64_t)block * (params->rays_per_thread > 0 ? params->rays_per_thread : 16);
     a.refill_min = params->refill_min > 0 ? params->refill_min : 8;
+    a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);

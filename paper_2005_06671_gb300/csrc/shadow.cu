@@ -16,30 +16,46 @@ __device__ __forceinline__ int64_t ray_count(const Tile& T, const Rays& R) {
     return R.mode == 0 ? (int64_t)T.nx * T.ny : R.n;
 }
 
-// Final value of one ray: re-evaluate the argmin sample in FP64 when the light
-// is not saturated, then apply the disc-occlusion formula (Eq. discfrac).
-__device__ __forceinline__ void finish_ray(const FwdArgs& a, int64_t r, const RayF& rf,
-                                           float best, int32_t bestj, int32_t nb, int32_t nl) {
+// cos(eps_p) of ray r's origin in float32 (relative error ~1e-7), enough to
+// decide whether its light is saturated.
+__device__ __forceinline__ float cos_elev_f32(const FwdArgs& a, int64_t r) {
+    float u, v;
+    if (a.R.mode == 0) {
+        const int64_t vv = r / a.T.nx;
+        u = (float)(r - vv * a.T.nx);
+        v = (float)vv;
+    } else {
+        u = a.R.uv[2 * r];
+        v = a.R.uv[2 * r + 1];
+    }
+    const float g = (float)a.T.g, R = (float)a.T.R;
+    const float X = (u - (float)a.T.cx) * g, Y = (v - (float)a.T.cy) * g;
+    const float se = (X * (float)a.T.sx + Y * (float)a.T.sy + R * (float)a.T.sz) *
+                     rsqrtf(X * X + Y * Y + R * R);
+    return sqrtf(fmaxf(0.0f, 1.0f - se * se));
+}
+
+// Final value of one ray: re-evaluate the argmin sample in FP64 unless the
+// light is certainly saturated (|c*| cos(eps) >= 1.001 alpha), then the
+// disc-occlusion formula (Eq. discfrac).
+__device__ __forceinline__ void finish_ray(const FwdArgs& a, int64_t r, float best,
+                                           int32_t bestj, int32_t nb, int32_t nl) {
     float light, cost;
     if (bestj < 0) {
         light = 1.0f;
         cost = INFINITY;
+    } else if (fabsf(best) * cos_elev_f32(a, r) >= 1.001f * a.T.alpha_f) {
+        light = best > 0.0f ? 1.0f : 0.0f;
+        cost = best;
     } else {
-        float d = best * rf.cos_e / a.T.alpha_f;
-        if (fabsf(d) < 1.001f) {
-            double up, vp, hp, href, ow[4];
-            int32_t oi0, oj0;
-            ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
-            Geom64 G;
-            geom64(a.T, up, vp, hp, G);
-            double c = leaf_cost64(a.T, G, bestj);
-            double dd = c * G.cos_e / a.T.alpha;
-            light = (float)disc_light64(dd);
-            cost = (float)c;
-        } else {
-            light = d > 0.0f ? 1.0f : 0.0f;
-            cost = best;
-        }
+        double up, vp, hp, href, ow[4];
+        int32_t oi0, oj0;
+        ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
+        Geom64 G;
+        geom64(a.T, up, vp, hp, G);
+        double c = leaf_cost64(a.T, G, bestj);
+        light = (float)disc_light64(c * G.cos_e / a.T.alpha);
+        cost = (float)c;
     }
     a.O.light[r] = light;
     a.O.argmin[r] = bestj;
@@ -50,13 +66,23 @@ __device__ __forceinline__ void finish_ray(const FwdArgs& a, int64_t r, const Ra
     }
 }
 
+template <bool kGrid>
 __device__ __forceinline__ void setup_ray(const FwdArgs& a, int64_t r, float span, RayF& rf) {
-    double up, vp, hp, href, ow[4];
-    int32_t oi0, oj0;
-    ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
+    double up, vp, hp, href;
+    if (kGrid) {
+        const int64_t v = r / a.T.nx, u = r - v * a.T.nx;
+        up = (double)u;
+        vp = (double)v;
+        hp = href = (double)a.T.h[v * a.T.pitch + u];
+    } else {
+        double ow[4];
+        int32_t oi0, oj0;
+        ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
+    }
     Geom64 G;
     geom64(a.T, up, vp, hp, G);
     make_rayf(a.T, G, href, span, rf);
+    if (kGrid) rf.X = 0.0f;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -74,11 +100,12 @@ constexpr unsigned kFull = 0xffffffffu;
 #endif
 
 // Scheduling shared by both forward kernels.  Block b owns rays
-// [b*rays_per_block, ...) (grid oversubscribes the SMs so the hardware block
-// scheduler balances them).  Each lane walks one ray; when at least
-// refill_min lanes of a warp are idle, those lanes take the next rays of the
-// block pool at once (ballot + one shared-memory atomic per warp), so lanes
-// whose rays finish early do not idle until the slowest lane is done.
+// [b*rays_per_block, ...) (the grid oversubscribes the SMs so the hardware
+// block scheduler balances them).  Each lane walks one ray.  A lane whose ray
+// is finished keeps its result in registers and waits; once at least
+// refill_min lanes of the warp are waiting (or all are), the warp services
+// them together: finished rays are written, and the waiting lanes draw the
+// next rays of the block pool (one shared-memory atomic per warp).
 struct BlockPool {
     int64_t lo;
     int32_t cnt;
@@ -89,24 +116,23 @@ __device__ __forceinline__ BlockPool block_pool(const FwdArgs& a, int32_t* s_nex
     BlockPool P;
     const int64_t n = ray_count(a.T, a.R);
     P.lo = (int64_t)blockIdx.x * a.rays_per_block;
-    int64_t c = n - P.lo;
+    const int64_t c = n - P.lo;
     P.cnt = (int32_t)(c < a.rays_per_block ? c : a.rays_per_block);
     return P;
 }
 
-// Returns the ray index this lane should start (or -1); updates `open`.
-__device__ __forceinline__ int64_t refill(const FwdArgs& a, const BlockPool& P, int32_t* s_next,
-                                          bool idle_lane, bool& open) {
-    const unsigned idle = __ballot_sync(kFull, idle_lane);
-    if (!open || idle == 0 || (idle != kFull && __popc(idle) < a.refill_min)) return -1;
+// Draw rays for this warp's lanes with r < 0; returns the new local index or -1.
+__device__ __forceinline__ int32_t draw(const BlockPool& P, int32_t* s_next, int32_t r,
+                                        bool& open) {
+    const unsigned idle = __ballot_sync(kFull, r < 0);
     const int nidle = __popc(idle);
     int base = 0;
-    if ((threadIdx.x & 31) == 0) base = atomicAdd(s_next, nidle);
+    if ((threadIdx.x & 31) == 0 && nidle > 0) base = atomicAdd(s_next, nidle);
     base = __shfl_sync(kFull, base, 0);
     if (base + nidle >= P.cnt) open = false;
-    if (!idle_lane) return -1;
+    if (r >= 0) return r;
     const int my = base + __popc(idle & lanemask_lt());
-    return my < P.cnt ? P.lo + my : -1;
+    return my < P.cnt ? my : -1;
 }
 
 // ---------------------------------------------------------------- descent
@@ -116,78 +142,82 @@ __device__ __forceinline__ int64_t refill(const FwdArgs& a, const BlockPool& P, 
 // evaluated sample by sample.  After a block, the walk continues at
 // s0 += 2^k with k = ctz(s0), the next block in near-to-far order, so samples
 // are evaluated in increasing j and a strict '<' keeps the smallest j among
-// equal costs.  Each loop iteration is exactly one probe per active lane.
-template <bool kCount>
+// equal costs.  Each loop iteration is exactly one probe per walking lane.
+// Blocks are aligned to their size, so for k = ctz(s0) the block may end past
+// j_hi; it is clipped.  The leaf level bounds the smallest block that gets a
+// bound probe: runs of 2^(kleaf+1) samples are evaluated directly.
+template <bool kCount, bool kGrid, bool kPoly>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(const FwdArgs a) {
-    __shared__ const float* s_ptr[kMaxLevels];
-    __shared__ int64_t s_pitch[kMaxLevels];
+    __shared__ LevelTab s_lev;
     __shared__ int32_t s_next;
     if (threadIdx.x < kMaxLevels) {
-        s_ptr[threadIdx.x] = a.P.ptr[threadIdx.x];
-        s_pitch[threadIdx.x] = a.P.pitch[threadIdx.x];
+        s_lev.ptr[threadIdx.x] = a.P.ptr[threadIdx.x];
+        s_lev.pitch[threadIdx.x] = (uint32_t)a.P.pitch[threadIdx.x];
     }
     const BlockPool P = block_pool(a, &s_next);
     __syncthreads();
     const float span = a.stats[0] - a.stats[1];
     const int32_t kleaf = a.kleaf, levels = a.P.levels;
 
-    int64_t r = -1;
+    int32_t r = -1;
+    bool done = false, open = true;
     RayF rf;
     float best = INFINITY;
     int32_t bestj = -1, nb = 0, nl = 0, s0 = 0, k = 0;
-    bool open = true;
     while (true) {
-        const int64_t nr = refill(a, P, &s_next, r < 0, open);
-        if (nr >= 0) {
-            r = nr;
-            setup_ray(a, r, span, rf);
-            best = INFINITY;
-            bestj = -1;
-            nb = nl = s0 = 0;
-            const int32_t K = rf.j_hi <= 1 ? 0 : 32 - __clz(rf.j_hi - 1);   // 2^K >= j_hi
-            k = K > kleaf ? K : 0;
-            if (rf.j_hi < rf.j_lo) {   // no usable sample
-                finish_ray(a, r, rf, best, bestj, 0, 0);
+        unsigned act = __ballot_sync(kFull, r >= 0 && !done);
+        if (act == 0 || (open && __popc(~act) >= a.refill_min)) {
+            if (done) {
+                finish_ray(a, P.lo + r, best, bestj, nb, nl);
                 r = -1;
+                done = false;
+            }
+            if (open) {
+                const int32_t nr = draw(P, &s_next, r, open);
+                if (nr >= 0 && r < 0) {
+                    r = nr;
+                    setup_ray<kGrid>(a, P.lo + r, span, rf);
+                    best = INFINITY;
+                    bestj = -1;
+                    nb = nl = s0 = 0;
+                    // While best is +inf every block on the left spine is split
+                    // without a bound being able to prune it, so the walk starts
+                    // directly with the first run of leaves (same order, same result).
+                    k = 0;
+                    if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
+                        finish_ray(a, P.lo + r, best, bestj, 0, 0);
+                        r = -1;
+                    }
+                }
+            }
+            act = __ballot_sync(kFull, r >= 0 && !done);
+            if (act == 0) {
+                if (!open) break;
+                continue;
             }
         }
-        if (__ballot_sync(kFull, r >= 0) == 0) {
-            if (!open) break;
-            continue;
-        }
-        if (r < 0) continue;
+        if (r < 0 || done) continue;
         const bool leaf = (k == 0);
-        int32_t ja = leaf ? s0 + 1 : max(s0 + 1, rf.j_lo);
-        int32_t jb = leaf ? s0 + 1 : min(s0 + (1 << k), rf.j_hi);
-        const bool valid = leaf ? (ja >= rf.j_lo) : (ja <= jb);
-        if (!valid) ja = jb = rf.j_lo;   // keep the probe in range; result unused
-        const float v = probe(a.T, s_ptr, s_pitch, levels, rf, ja, jb, leaf);
-        bool advance = true;
-        if (valid) {
-            if (leaf) {
-                if (kCount) ++nl;
-                if (v < best) {
-                    best = v;
-                    bestj = ja;
-                }
-            } else {
-                if (kCount) ++nb;
-                if (!(v > best)) {
-                    k = (k - 1 > kleaf) ? k - 1 : 0;
-                    advance = false;
-                }
-            }
+        const int32_t s1 = s0 + 1;
+        int32_t ja = leaf ? s1 : max(s1, rf.j_lo);
+        int32_t jb = leaf ? s1 : min(s0 + (1 << k), rf.j_hi);
+        const bool valid = leaf ? (s1 >= rf.j_lo) : (ja <= jb);
+        ja = valid ? ja : rf.j_lo;
+        jb = valid ? jb : rf.j_lo;
+        const float v = probe<kGrid, kPoly>(a.T, s_lev, levels, rf, ja, jb, leaf);
+        const bool improve = valid && leaf && (v < best);
+        best = improve ? v : best;
+        bestj = improve ? ja : bestj;
+        const bool descend = valid && !leaf && !(v > best);
+        if (kCount) {
+            nl += (valid && leaf) ? 1 : 0;
+            nb += (valid && !leaf) ? 1 : 0;
         }
-        if (advance) {
-            s0 += 1 << k;
-            if (s0 >= rf.j_hi) {
-                finish_ray(a, r, rf, best, bestj, nb, nl);
-                r = -1;
-            } else {
-                k = __ffs(s0) - 1;
-                if (k <= kleaf) k = 0;
-            }
-        }
+        const int32_t s_adv = s0 + (1 << k);
+        const int32_t k_adv = __ffs(s_adv) - 1;
+        s0 = descend ? s0 : s_adv;
+        k = descend ? ((k - 1 > kleaf) ? k - 1 : 0) : ((k_adv <= kleaf) ? 0 : k_adv);
+        done = !descend && (s_adv >= rf.j_hi);
     }
 }
 
@@ -197,7 +227,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
 // g(t) = (H(t) - max h - G)/t is non-decreasing and bounds every later
 // sample's cost from below; once g(t_j) >= best no later sample can win.
 // G = 3 guards covers the float32 rounding of both sides.
-template <bool kCount>
+template <bool kCount, bool kGrid, bool kPoly>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel(const FwdArgs a) {
     __shared__ int32_t s_next;
     const BlockPool P = block_pool(a, &s_next);
@@ -206,53 +236,62 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel
     const float span = a.stats[0] - a.stats[1];
     const bool allow_exit = !(a.flags & 0x2u);
 
-    int64_t r = -1;
+    int32_t r = -1;
+    bool done = false, open = true;
     RayF rf;
     float best = INFINITY, hmax_rel = 0.0f, G = 0.0f;
     int32_t bestj = -1, nl = 0, j = 0;
-    bool exit_ok = false, open = true;
+    bool exit_ok = false;
     while (true) {
-        const int64_t nr = refill(a, P, &s_next, r < 0, open);
-        if (nr >= 0) {
-            r = nr;
-            setup_ray(a, r, span, rf);
-            best = INFINITY;
-            bestj = -1;
-            nl = 0;
-            j = rf.j_lo;
-            hmax_rel = hmax - rf.href;
-            exit_ok = allow_exit && (rf.X <= hmax_rel);
-            const float tJ = (float)rf.j_hi * a.T.delta_f;
-            const float rb = fmaxf(rise_bound(rf, tJ), 0.25f * rf.B * rf.B * rf.inv_rho);
-            G = 3.0f * kGuardRel * (rf.guard0 + fabsf(hmax_rel) + rb);
-            if (rf.j_hi < rf.j_lo) {
-                finish_ray(a, r, rf, best, bestj, 0, 0);
+        unsigned act = __ballot_sync(kFull, r >= 0 && !done);
+        if (act == 0 || (open && __popc(~act) >= a.refill_min)) {
+            if (done) {
+                finish_ray(a, P.lo + r, best, bestj, 0, nl);
                 r = -1;
+                done = false;
+            }
+            if (open) {
+                const int32_t nr = draw(P, &s_next, r, open);
+                if (nr >= 0 && r < 0) {
+                    r = nr;
+                    setup_ray<kGrid>(a, P.lo + r, span, rf);
+                    best = INFINITY;
+                    bestj = -1;
+                    nl = 0;
+                    j = rf.j_lo;
+                    hmax_rel = hmax - rf.href;
+                    exit_ok = allow_exit && (rf.X <= hmax_rel);
+                    const float tJ = (float)rf.j_hi * a.T.delta_f;
+                    const float rb = fmaxf(rise_bound(rf, tJ),
+                                           0.5f * rf.B * rf.B * rf.inv_2rho);
+                    G = 3.0f * kGuardRel * (rf.guard0 + fabsf(hmax_rel) + rb);
+                    if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
+                        finish_ray(a, P.lo + r, best, bestj, 0, 0);
+                        r = -1;
+                    }
+                }
+            }
+            act = __ballot_sync(kFull, r >= 0 && !done);
+            if (act == 0) {
+                if (!open) break;
+                continue;
             }
         }
-        if (__ballot_sync(kFull, r >= 0) == 0) {
-            if (!open) break;
-            continue;
-        }
-        if (r < 0) continue;
+        if (r < 0 || done) continue;
         float rise;
-        const float c = leaf_cost(a.T, rf, j, &rise);
+        const float c = leaf_cost<kGrid, kPoly>(a.T, rf, j, rise);
         if (kCount) ++nl;
-        if (c < best) {
-            best = c;
-            bestj = j;
-        }
-        bool done = (j >= rf.j_hi);
-        if (!done && exit_ok && (j & 3) == 0) {
+        const bool improve = c < best;
+        best = improve ? c : best;
+        bestj = improve ? j : bestj;
+        bool stop = (j >= rf.j_hi);
+        if (exit_ok && (j & 3) == 0) {
             const float t = __fmul_rn((float)j, a.T.delta_f);
-            const float g = (((rf.X + rise) - hmax_rel) - G) / t;
-            done = (g >= best);
+            const float h = kGrid ? rise : rf.X + rise;
+            stop = stop || ((h - hmax_rel) - G) / t >= best;
         }
         ++j;
-        if (done) {
-            finish_ray(a, r, rf, best, bestj, 0, nl);
-            r = -1;
-        }
+        done = stop;
     }
 }
 
@@ -378,22 +417,40 @@ static int pool_grid(const FwdArgs& a) {
     return (int)((n + a.rays_per_block - 1) / a.rays_per_block);
 }
 
+template <template <bool, bool, bool> class Launch>
+static cudaError_t dispatch(const FwdArgs& a, int block, cudaStream_t s) {
+    const bool cnt = a.O.counters != nullptr, grid = a.R.mode == 0, poly = a.poly != 0;
+    const int g = pool_grid(a);
+    if (cnt) {
+        if (grid) return poly ? Launch<true, true, true>::go(a, g, block, s) : Launch<true, true, false>::go(a, g, block, s);
+        return poly ? Launch<true, false, true>::go(a, g, block, s) : Launch<true, false, false>::go(a, g, block, s);
+    }
+    if (grid) return poly ? Launch<false, true, true>::go(a, g, block, s) : Launch<false, true, false>::go(a, g, block, s);
+    return poly ? Launch<false, false, true>::go(a, g, block, s) : Launch<false, false, false>::go(a, g, block, s);
+}
+
+template <bool C, bool G, bool P>
+struct DpLaunch {
+    static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
+        dp_forward_kernel<C, G, P><<<grid, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+template <bool C, bool G, bool P>
+struct UniLaunch {
+    static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
+        uniform_forward_kernel<C, G, P><<<grid, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
 cudaError_t launch_dp_forward(const FwdArgs& a, int block, cudaStream_t s) {
-    const int grid = pool_grid(a);
-    if (a.O.counters)
-        dp_forward_kernel<true><<<grid, block, 0, s>>>(a);
-    else
-        dp_forward_kernel<false><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    return dispatch<DpLaunch>(a, block, s);
 }
 
 cudaError_t launch_uniform_forward(const FwdArgs& a, int block, cudaStream_t s) {
-    const int grid = pool_grid(a);
-    if (a.O.counters)
-        uniform_forward_kernel<true><<<grid, block, 0, s>>>(a);
-    else
-        uniform_forward_kernel<false><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    return dispatch<UniLaunch>(a, block, s);
 }
 
 cudaError_t launch_backward(const BwdArgs& a, int block, cudaStream_t s) {

@@ -77,26 +77,21 @@ struct Geom64 {
     double ow[4];              // origin bilinear weights (i0,j0),(i0+1,j0),(i0,j0+1),(i0+1,j0+1)
 };
 
-// float32 per-ray state of the hot loop.
+// float32 per-ray state of the hot loop (kept small: it lives in registers
+// for the whole walk of a ray).
 struct RayF {
     int32_t iu0, iv0;          // integer part of the origin position
-    float fu0, fv0;            // fractional part
-    float u0, v0;              // origin position (float) for block footprints
+    float u0, v0;              // origin position (exact: integer or the input float)
     float au_hi, au_lo, av_hi, av_lo;  // per-sample slope split so that j*a_hi is exact
-    float au, av;              // (float) slopes
     float b;                   // projective coefficient
     float B;                   // 2 rho sin_e
-    float rho;                 // R + h_p
     float inv_2rho, inv_rho2;  // 1/(2 rho), 1/rho^2
-    float inv_rho;
-    float X;                   // h_p - h_ref
+    float X;                   // h_p - h_ref (0 in grid mode)
     float href;
     float tv;                  // distance of the lowest ray point (sin_e < 0), else -1
     float guard0;              // |X| + height span of the tile
     float pos_eps;             // footprint margin covering float32 block-end positions
-    float cos_e;
     int32_t j_lo, j_hi;        // usable sample range (empty when j_lo > j_hi)
-    int32_t exact_rise;        // 1: the rise series may not converge fast enough
 };
 
 // ------------------------------------------------------------------ helpers
@@ -213,43 +208,33 @@ __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double
     double iu = floor(G.up), iv = floor(G.vp);
     r.iu0 = (int32_t)iu;
     r.iv0 = (int32_t)iv;
-    r.fu0 = (float)(G.up - iu);
-    r.fv0 = (float)(G.vp - iv);
     r.u0 = (float)G.up;
     r.v0 = (float)G.vp;
     split8(G.Au, r.au_hi, r.au_lo);
     split8(G.Av, r.av_hi, r.av_lo);
-    r.au = (float)G.Au;
-    r.av = (float)G.Av;
     r.b = (float)G.b;
-    double B = 2.0 * G.rho * G.sin_e;
-    r.B = (float)B;
-    r.rho = (float)G.rho;
+    r.B = (float)(2.0 * G.rho * G.sin_e);
     r.inv_2rho = (float)(0.5 / G.rho);
     r.inv_rho2 = (float)(1.0 / (G.rho * G.rho));
-    r.inv_rho = 2.0f * r.inv_2rho;
     r.X = (float)(G.hp - href);
     r.href = (float)href;
     r.tv = G.sin_e < 0.0 ? (float)(-G.rho * G.sin_e) : -1.0f;
     r.guard0 = fabsf(r.X) + span;
-    r.cos_e = (float)G.cos_e;
     sample_range(T, G, r.j_lo, r.j_hi);
-    // |x| = |t (B + t)| / rho^2 over the ray; the 5-term series of the rise is
-    // used when |x| <= 1/32 (truncation < 1e-9 relative)
-    double tJ = (double)max(r.j_hi, 1) * T.delta;
-    double wmax = fmax(fabs(tJ * (B + tJ)), 0.25 * B * B);
-    r.exact_rise = (wmax / (G.rho * G.rho) > 0.03125) ? 1 : 0;
     // float32 block-end positions u0 + a*tau err by <= ulp(coordinate) plus
     // ~3 ulp of a*tau; the margin takes 4x that, plus 1e-3 texel
-    float amax = fmaxf(fabsf(r.au), fabsf(r.av));
+    float amax = fmaxf(fabsf((float)G.Au), fabsf((float)G.Av));
     r.pos_eps = 1e-3f + 5e-7f * (float)(T.nx + T.ny) + 8e-7f * amax * (float)max(r.j_hi, 1);
 }
 
 // ------------------------------------------------------------ float32 leaf
 // Every operation that produces a sample value is an explicitly rounded
-// intrinsic (__fadd_rn, __fmul_rn, __fmaf_rn, __fdiv_rn, __fsqrt_rn), which the
-// compiler never contracts or reorders: the value is the same bits in every
-// kernel and inlining context that evaluates it.
+// intrinsic (__fadd_rn, __fmul_rn, __fmaf_rn, ...), which the compiler never
+// contracts or reorders: the value is the same bits in every kernel and
+// inlining context that evaluates it.  Template flags only remove operations
+// that are exact no-ops for the specialised case (x + 0, grid origins).
+//   kGrid: rays start at texel centres (fractional origin 0, X = 0).
+//   kPoly: the rise series converges for every ray of the launch.
 struct Pos {
     int32_t i;
     float f;
@@ -262,14 +247,18 @@ __device__ __forceinline__ float corr_of(const RayF& r, float jf) {
 
 // Texel coordinate of sample j along one axis: integer part exact, fraction
 // accurate to ~1e-7 texel.  Base clamped to [0, n-2] (the fraction absorbs it).
-__device__ __forceinline__ Pos axis_pos(int32_t i0, float f0, float a_hi, float a_lo, float a,
+template <bool kGrid>
+__device__ __forceinline__ Pos axis_pos(int32_t i0, float u0, float a_hi, float a_lo,
                                         float corr, float jf, int32_t n) {
     float p = __fmul_rn(jf, a_hi);       // exact: a_hi has <= 8 significant bits
     float kp = floorf(p);
     float fp = __fsub_rn(p, kp);         // exact
-    float s = __fadd_rn(__fadd_rn(f0, fp), __fmaf_rn(jf, a_lo, -__fmul_rn(a, corr)));
+    float a = __fadd_rn(a_hi, a_lo);
+    float tail = __fmaf_rn(jf, a_lo, -__fmul_rn(a, corr));
+    float s = kGrid ? __fadd_rn(fp, tail)
+                    : __fadd_rn(__fadd_rn(__fsub_rn(u0, (float)i0), fp), tail);
     float fs = floorf(s);
-    int32_t i = i0 + (int32_t)kp + (int32_t)fs;
+    int32_t i = i0 + __float2int_rz(kp) + __float2int_rz(fs);
     float f = __fsub_rn(s, fs);
     int32_t ic = min(max(i, 0), n - 2);
     f = __fadd_rn(f, (float)(i - ic));
@@ -287,12 +276,16 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // rise(t) = |p + t s| - |p| = w / (rho + sqrt(rho^2 + w)), w = t (2 rho sin_e + t),
 // without cancellation.  With x = w / rho^2 this is (w / 2 rho) * 2/(1 + sqrt(1 + x))
-// = (w / 2 rho) (1 - x/4 + x^2/8 - 5x^3/64 + 7x^4/128 - ...); for |x| <= 1/32 the
-// truncation error is < 1e-9 relative, else the closed form is used.
+// = (w / 2 rho) (1 - x/4 + x^2/8 - 5x^3/64 + 7x^4/128 - ...); the host selects
+// the series (kPoly) only when |x| <= 1/32 for every ray (truncation < 1e-9
+// relative), else the closed form is used.
+template <bool kPoly>
 __device__ __forceinline__ float rise_of(const RayF& r, float t) {
     float w = __fmul_rn(t, __fadd_rn(r.B, t));
-    if (r.exact_rise)
-        return __fdiv_rn(w, __fadd_rn(r.rho, __fsqrt_rn(__fmaf_rn(r.rho, r.rho, w))));
+    if (!kPoly) {
+        float rho = __fdiv_rn(0.5f, r.inv_2rho);
+        return __fdiv_rn(w, __fadd_rn(rho, __fsqrt_rn(__fmaf_rn(rho, rho, w))));
+    }
     float x = __fmul_rn(w, r.inv_rho2);
     float p = __fmaf_rn(x, 0.0546875f, -0.078125f);
     p = __fmaf_rn(x, p, 0.125f);
@@ -301,9 +294,9 @@ __device__ __forceinline__ float rise_of(const RayF& r, float t) {
     return __fmul_rn(__fmul_rn(w, r.inv_2rho), p);
 }
 
-// upper bound of |rise(t)| without a square root
+// upper bound of |rise(t)| without a square root: |w| / rho
 __device__ __forceinline__ float rise_bound(const RayF& r, float t) {
-    return fabsf(t * (r.B + t)) * r.inv_rho;
+    return fabsf(t * (r.B + t)) * (2.0f * r.inv_2rho);
 }
 
 __device__ __forceinline__ float bilerp_rn(float d00, float d10, float d01, float d11, float fu,
@@ -318,36 +311,45 @@ __device__ __forceinline__ float inv_t(const Tile& T, float jf) {
     return __fmul_rn(T.inv_delta_f, rcp_approx(jf));
 }
 
-__device__ __forceinline__ const float* cell_ptr(const float* base, int64_t pitch, int32_t x,
+// Element offsets stay below 2^32 (the host checks pitch * ny <= 2^32).
+__device__ __forceinline__ const float* cell_ptr(const float* base, uint32_t pitch, int32_t x,
                                                  int32_t y) {
-    return base + ((int64_t)y * pitch + x);
+    return base + ((uint32_t)y * pitch + (uint32_t)x);
 }
 
 // Cost of sample j (float32); the uniform kernel's sample value.  probe() with
 // leaf == true returns the same bits.
+template <bool kGrid, bool kPoly>
 __device__ __forceinline__ float leaf_cost(const Tile& T, const RayF& r, int32_t j,
-                                           float* rise_out = nullptr) {
-    float jf = (float)j;
-    float corr = corr_of(r, jf);
-    Pos pu = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, corr, jf, T.nx);
-    Pos pv = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, corr, jf, T.ny);
-    float t = __fmul_rn(jf, T.delta_f);
-    float rise = rise_of(r, t);
-    if (rise_out) *rise_out = rise;
-    const float* p = cell_ptr(T.h, T.pitch, pu.i, pv.i);
-    float d00 = __fsub_rn(__ldg(p), r.href), d10 = __fsub_rn(__ldg(p + 1), r.href);
-    float d01 = __fsub_rn(__ldg(p + T.pitch), r.href);
-    float d11 = __fsub_rn(__ldg(p + T.pitch + 1), r.href);
-    float hb = bilerp_rn(d00, d10, d01, d11, pu.f, pv.f);
-    return __fmul_rn(__fsub_rn(__fadd_rn(r.X, rise), hb), inv_t(T, jf));
+                                           float& rise) {
+    const float jf = (float)j;
+    const float corr = corr_of(r, jf);
+    const Pos pu = axis_pos<kGrid>(r.iu0, r.u0, r.au_hi, r.au_lo, corr, jf, T.nx);
+    const Pos pv = axis_pos<kGrid>(r.iv0, r.v0, r.av_hi, r.av_lo, corr, jf, T.ny);
+    const float t = __fmul_rn(jf, T.delta_f);
+    rise = rise_of<kPoly>(r, t);
+    const uint32_t pitch = (uint32_t)T.pitch;
+    const float* p = cell_ptr(T.h, pitch, pu.i, pv.i);
+    const float d00 = __fsub_rn(__ldg(p), r.href), d10 = __fsub_rn(__ldg(p + 1), r.href);
+    const float d01 = __fsub_rn(__ldg(p + pitch), r.href);
+    const float d11 = __fsub_rn(__ldg(p + pitch + 1), r.href);
+    const float hb = bilerp_rn(d00, d10, d01, d11, pu.f, pv.f);
+    const float h = kGrid ? rise : __fadd_rn(r.X, rise);
+    return __fmul_rn(__fsub_rn(h, hb), inv_t(T, jf));
 }
 
 // float32 texel position of sample j for block footprints (error <= pos_eps)
 __device__ __forceinline__ void block_end(const RayF& r, float jf, float& u, float& v) {
     float tau = __fdividef(jf, __fmaf_rn(jf, r.b, 1.0f));
-    u = __fmaf_rn(r.au, tau, r.u0);
-    v = __fmaf_rn(r.av, tau, r.v0);
+    u = __fmaf_rn(__fadd_rn(r.au_hi, r.au_lo), tau, r.u0);
+    v = __fmaf_rn(__fadd_rn(r.av_hi, r.av_lo), tau, r.v0);
 }
+
+// Levels of the maximum mipmap as a kernel sees them (shared memory copy).
+struct LevelTab {
+    const float* ptr[kMaxLevels];
+    uint32_t pitch[kMaxLevels];
+};
 
 // One probe of the descent, a single code path for both kinds so that a warp
 // whose lanes mix them stays converged:
@@ -360,49 +362,50 @@ __device__ __forceinline__ void block_end(const RayF& r, float jf, float& u, flo
 //    widened by pos_eps); the guard 2^-19 (|X| + |rise| + |M - h_ref| + span)
 //    covers every float32 rounding of the leaf and of the bound, so no sample
 //    that could win is skipped.
-__device__ __forceinline__ float probe(const Tile& T, const float* const* lev_ptr,
-                                       const int64_t* lev_pitch, int32_t levels, const RayF& r,
-                                       int32_t ja, int32_t jb, bool leaf) {
+template <bool kGrid, bool kPoly>
+__device__ __forceinline__ float probe(const Tile& T, const LevelTab& L, int32_t levels,
+                                       const RayF& r, int32_t ja, int32_t jb, bool leaf) {
     const float fa = (float)ja, fb = (float)jb;
     // leaf position (the sample's bilinear cell)
     const float ca = corr_of(r, fa);
-    const Pos ua = axis_pos(r.iu0, r.fu0, r.au_hi, r.au_lo, r.au, ca, fa, T.nx);
-    const Pos va = axis_pos(r.iv0, r.fv0, r.av_hi, r.av_lo, r.av, ca, fa, T.ny);
+    const Pos ua = axis_pos<kGrid>(r.iu0, r.u0, r.au_hi, r.au_lo, ca, fa, T.nx);
+    const Pos va = axis_pos<kGrid>(r.iv0, r.v0, r.av_hi, r.av_lo, ca, fa, T.ny);
     // block footprint box from both ends
     float xa, ya, xb, yb;
     block_end(r, fa, xa, ya);
     block_end(r, fb, xb, yb);
     const float e = r.pos_eps;
-    int32_t x0 = max((int32_t)floorf(fminf(xa, xb) - e), 0);
-    int32_t x1 = min((int32_t)floorf(fmaxf(xa, xb) + e) + 1, T.nx - 1);
-    int32_t y0 = max((int32_t)floorf(fminf(ya, yb) - e), 0);
-    int32_t y1 = min((int32_t)floorf(fmaxf(ya, yb) + e) + 1, T.ny - 1);
+    int32_t x0 = max(__float2int_rd(fminf(xa, xb) - e), 0);
+    int32_t x1 = min(__float2int_rd(fmaxf(xa, xb) + e) + 1, T.nx - 1);
+    int32_t y0 = max(__float2int_rd(fminf(ya, yb) - e), 0);
+    int32_t y1 = min(__float2int_rd(fmaxf(ya, yb) + e) + 1, T.ny - 1);
     const int32_t ext = max(x1 - x0, y1 - y0);
     int32_t m = ext <= 1 ? 0 : 31 - __clz(ext);
-    if (((x1 >> m) - (x0 >> m)) > 1 || ((y1 >> m) - (y0 >> m)) > 1) ++m;
+    m += (((x1 >> m) - (x0 >> m)) > 1 || ((y1 >> m) - (y0 >> m)) > 1) ? 1 : 0;
     m = min(m, levels - 1);
-    if (leaf) {
-        x0 = ua.i; x1 = ua.i + 1; y0 = va.i; y1 = va.i + 1; m = 0;
-    }
-    const int64_t pm = lev_pitch[m];
-    const float* p = cell_ptr(lev_ptr[m], pm, x0 >> m, y0 >> m);
-    const int32_t dx = (x1 >> m) - (x0 >> m);
-    const int64_t dy = ((y1 >> m) - (y0 >> m)) * pm;
+    m = leaf ? 0 : m;
+    x0 = leaf ? ua.i : x0;
+    y0 = leaf ? va.i : y0;
+    x1 = leaf ? ua.i + 1 : x1;
+    y1 = leaf ? va.i + 1 : y1;
+    const uint32_t pm = L.pitch[m];
+    const float* p = cell_ptr(L.ptr[m], pm, x0 >> m, y0 >> m);
+    const uint32_t dx = (uint32_t)((x1 >> m) - (x0 >> m));
+    const uint32_t dy = (uint32_t)((y1 >> m) - (y0 >> m)) * pm;
     const float d00 = __fsub_rn(__ldg(p), r.href);
     const float d10 = __fsub_rn(__ldg(p + dx), r.href);
     const float d01 = __fsub_rn(__ldg(p + dy), r.href);
     const float d11 = __fsub_rn(__ldg(p + dy + dx), r.href);
     const float ta = __fmul_rn(fa, T.delta_f), tb = __fmul_rn(fb, T.delta_f);
     const float tstar = (leaf || !(r.tv > ta)) ? ta : fminf(r.tv, tb);
-    const float rise = rise_of(r, tstar);
+    const float rise = rise_of<kPoly>(r, tstar);
     const float V = leaf ? bilerp_rn(d00, d10, d01, d11, ua.f, va.f)
                          : fmaxf(fmaxf(d00, d10), fmaxf(d01, d11));
-    float num = __fsub_rn(__fadd_rn(r.X, rise), V);
-    float den_j = fa;
-    if (!leaf) {
-        num = __fsub_rn(num, kGuardRel * (r.guard0 + fabsf(V) + rise_bound(r, tb) + fabsf(rise)));
-        den_j = num >= 0.0f ? fb : fa;
-    }
+    const float h = kGrid ? rise : __fadd_rn(r.X, rise);
+    const float num0 = __fsub_rn(h, V);
+    const float guard = kGuardRel * (r.guard0 + fabsf(V) + rise_bound(r, tb) + fabsf(rise));
+    const float num = leaf ? num0 : __fsub_rn(num0, guard);
+    const float den_j = (leaf || !(num >= 0.0f)) ? fa : fb;
     return __fmul_rn(num, inv_t(T, den_j));
 }
 

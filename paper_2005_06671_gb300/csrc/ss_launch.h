@@ -30,7 +30,8 @@ struct FwdArgs {
     int32_t kleaf;
     uint32_t flags;
     int64_t rays_per_block;   // rays owned by one block
-    int32_t refill_min;       // idle lanes that trigger a warp refill
+    int32_t refill_min;       // waiting lanes that trigger a warp service
+    int32_t poly;             // 1: the rise series is valid for every ray
 };
 
 struct BwdArgs {
