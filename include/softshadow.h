@@ -111,6 +111,10 @@ typedef struct {
     int32_t refill_min;    /* forward kernels: a warp's idle lanes take new
                               rays once at least this many are idle, in
                               [0, 32]; 0 = default (8)                         */
+    int32_t ray_tile_w;    /* grid-mode rays: 0 = a block (batch: a warp) takes
+                              runs of consecutive ray ids; w > 0 = rectangles
+                              of w x (rays / w) texels (w must divide the
+                              block's or chunk's ray count)                   */
     int32_t reserved;      /* must be 0                                        */
 } ss_params;
 
@@ -189,6 +193,44 @@ ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, cons
                              const ss_params* params, const int32_t* argmin,
                              const float* grad_light, float* grad_h, double* grad_sun,
                              ss_stream_t stream);
+
+/* ------------------------------------------------------------- batched
+ * Many (heightfield tile, sun) instances of uneven sizes in one persistent
+ * launch: the maximum mipmaps of all instances are built, then one kernel with
+ * a device-side work queue (a chunk counter in the workspace; no device-side
+ * waits) walks every ray of every instance with the exact descent of
+ * ss_shadow_forward, giving the same per-ray outputs bit for bit.  The nearest
+ * counterpart in the paper is drawing many visible tiles per frame (Sec. 3.3,
+ * virtual texturing; Sec. 6.3).  Grid-mode rays (one per texel centre),
+ * gnomonic tiles.  params (max_len_m, step_texels, ...) apply to every item. */
+typedef struct {
+    ss_heightfield hf;     /* device heights; projection SS_PROJ_GNOMONIC       */
+    float* mip;            /* device, ss_maxmip_bytes(hf.nx, hf.ny); written    */
+    ss_sun sun;
+    ss_outputs out;        /* device arrays of hf.nx * hf.ny entries            */
+} ss_batch_item;
+
+/* Bytes of the device workspace a batch of n_items needs (caller-allocated;
+ * holds the instance descriptors and the work-queue counter). */
+size_t ss_batch_workspace_bytes(int32_t n_items);
+
+/* Enqueue one batch on `stream`: descriptor upload (from host memory, copied
+ * before the call returns), queue reset, mipmap builds, persistent kernel.
+ * The workspace must not be in use by another batch in flight. */
+ss_status ss_batch_submit(const ss_batch_item* items, int32_t n_items, const ss_params* params,
+                          void* workspace, size_t workspace_bytes, ss_stream_t stream);
+
+/* A batch captured once into a CUDA graph and replayed: plan_create uploads the
+ * descriptors (synchronously) and captures queue reset + mipmap builds +
+ * persistent kernel; plan_launch replays the graph on `stream` (the items'
+ * buffers and the workspace must stay valid while the plan exists, and
+ * replays of one plan must not overlap). */
+typedef struct ss_batch_plan ss_batch_plan;
+ss_status ss_batch_plan_create(const ss_batch_item* items, int32_t n_items,
+                               const ss_params* params, void* workspace, size_t workspace_bytes,
+                               ss_batch_plan** plan);
+ss_status ss_batch_plan_launch(ss_batch_plan* plan, ss_stream_t stream);
+ss_status ss_batch_plan_destroy(ss_batch_plan* plan);
 
 #ifdef __cplusplus
 }

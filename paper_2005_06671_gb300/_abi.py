@@ -36,7 +36,11 @@ class SSSun(ctypes.Structure):
 class SSParams(ctypes.Structure):
     _fields_ = [("max_len_m", c_f64), ("step_texels", c_f64), ("flags", c_u32),
                 ("block_threads", c_i32), ("leaf_level", c_i32), ("rays_per_thread", c_i32),
-                ("refill_min", c_i32), ("reserved", c_i32)]
+                ("refill_min", c_i32), ("ray_tile_w", c_i32), ("reserved", c_i32)]
+
+
+class SSBatchItem(ctypes.Structure):
+    pass
 
 
 class SSRays(ctypes.Structure):
@@ -45,6 +49,9 @@ class SSRays(ctypes.Structure):
 
 class SSOutputs(ctypes.Structure):
     _fields_ = [("light", c_vp), ("argmin", c_vp), ("cost", c_vp), ("counters", c_vp)]
+
+
+SSBatchItem._fields_ = [("hf", SSHeightfield), ("mip", c_vp), ("sun", SSSun), ("out", SSOutputs)]
 
 
 P = ctypes.POINTER
@@ -62,6 +69,12 @@ _SIGNATURES = {
                                   P(SSOutputs), c_vp]),
     "ss_shadow_backward": (c_i32, [P(SSHeightfield), P(SSRays), P(SSSun), P(SSParams), c_vp,
                                    c_vp, c_vp, c_vp, c_vp]),
+    "ss_batch_workspace_bytes": (ctypes.c_size_t, [c_i32]),
+    "ss_batch_submit": (c_i32, [c_vp, c_i32, P(SSParams), c_vp, ctypes.c_size_t, c_vp]),
+    "ss_batch_plan_create": (c_i32, [c_vp, c_i32, P(SSParams), c_vp, ctypes.c_size_t,
+                                     P(c_vp)]),
+    "ss_batch_plan_launch": (c_i32, [c_vp, c_vp]),
+    "ss_batch_plan_destroy": (c_i32, [c_vp]),
 }
 
 _lock = threading.Lock()

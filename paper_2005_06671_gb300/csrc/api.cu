@@ -6,8 +6,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
 #include "../../include/softshadow.h"
+#include "ss_batch.h"
 #include "ss_launch.h"
+#include "ss_walk.cuh"
 
 namespace {
 
@@ -52,6 +56,7 @@ ss_status check_params(const ss_params* p, double g, int32_t* J, double* delta) 
     if (p->leaf_level < -1 || p->leaf_level > 16) return SS_ERR_INVALID_ARG;
     if (p->rays_per_thread < 0 || p->rays_per_thread > 4096) return SS_ERR_INVALID_ARG;
     if (p->refill_min < 0 || p->refill_min > 32) return SS_ERR_INVALID_ARG;
+    if (p->ray_tile_w < 0 || p->ray_tile_w > SS_MAX_DIM) return SS_ERR_INVALID_ARG;
     if (p->reserved != 0) return SS_ERR_INVALID_ARG;
     double st = p->step_texels == 0.0 ? 0.5 : p->step_texels;
     double d = st * g;
@@ -176,6 +181,8 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.rays_per_block = (int64_t)block * (params->rays_per_thread > 0 ? params->rays_per_thread : 16);
     a.refill_min = params->refill_min > 0 ? params->refill_min : 8;
     a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
+    a.tile_w = params->ray_tile_w;
+    if (a.tile_w > 0 && a.rays_per_block % a.tile_w != 0) return SS_ERR_INVALID_ARG;
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);
@@ -183,7 +190,97 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     return SS_OK;
 }
 
+// ------------------------------------------------------------------ batch
+struct BatchPrep {
+    std::vector<unsigned char> image;   // workspace contents after the header
+    ss::BatchArgs args{};
+    std::vector<ss::MipLayout> layouts;
+    int block = 256;
+    bool count = false;
+};
+
+ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* params, void* ws,
+                        size_t ws_bytes, BatchPrep& B) {
+    if (!items || !params || !ws) return SS_ERR_INVALID_ARG;
+    if (n < 1 || n > (1 << 20)) return SS_ERR_BAD_SIZE;
+    if (ws_bytes < ss::batch_workspace_bytes(n)) return SS_ERR_OUT_OF_MEMORY;
+    if (params->block_threads != 0 &&
+        (params->block_threads < 32 || params->block_threads > 256 || params->block_threads % 32))
+        return SS_ERR_INVALID_ARG;
+    B.block = params->block_threads ? params->block_threads : 256;
+    B.count = (params->flags & SS_FLAG_COUNT_SAMPLES) != 0;
+    const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : 16;
+    const int32_t chunk = 32 * rpt;
+    const int32_t tile_w = params->ray_tile_w;
+    if (tile_w > 0 && chunk % tile_w != 0) return SS_ERR_INVALID_ARG;
+    const size_t desc_bytes = ss::align256((size_t)n * sizeof(ss::BatchItemDesc));
+    B.image.assign(desc_bytes + (size_t)(n + 1) * sizeof(int64_t), 0);
+    auto* descs = reinterpret_cast<ss::BatchItemDesc*>(B.image.data());
+    auto* prefix = reinterpret_cast<int64_t*>(B.image.data() + desc_bytes);
+    B.layouts.resize(n);
+    prefix[0] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const ss_batch_item& it = items[i];
+        ss_status st = check_tile(&it.hf, 2);
+        if (st != SS_OK) return st;
+        if (it.hf.projection != SS_PROJ_GNOMONIC) return SS_ERR_UNSUPPORTED;
+        if ((st = check_sun(&it.sun)) != SS_OK) return st;
+        int32_t J;
+        double delta;
+        if ((st = check_params(params, it.hf.texel_m, &J, &delta)) != SS_OK) return st;
+        if (!it.mip || !it.out.light || !it.out.argmin) return SS_ERR_INVALID_ARG;
+        if (B.count && !it.out.counters) return SS_ERR_INVALID_ARG;
+        if (!ss::mip_layout(it.hf.nx, it.hf.ny, &B.layouts[i])) return SS_ERR_BAD_SIZE;
+        ss::BatchItemDesc& d = descs[i];
+        d.T = make_tile(&it.hf, &it.sun, J, delta);
+        const ss::Pyramid P = make_pyramid(&it.hf, it.mip, B.layouts[i]);
+        for (int l = 0; l < ss::kMaxLevels; ++l) {
+            d.L.ptr[l] = l < P.levels ? P.ptr[l] : nullptr;
+            d.L.pitch[l] = l < P.levels ? (uint32_t)P.pitch[l] : 0u;
+        }
+        d.levels = P.levels;
+        d.O.light = it.out.light;
+        d.O.argmin = it.out.argmin;
+        d.O.cost = it.out.cost;
+        d.O.counters = B.count ? it.out.counters : nullptr;
+        d.stats = it.mip + B.layouts[i].stats_offset;
+        d.n_rays = (int64_t)it.hf.nx * it.hf.ny;
+        d.poly = rise_series_ok(&it.hf, &it.sun, J * delta, SS_RAYS_GRID) ? 1 : 0;
+        d.tile_w = tile_w;
+        prefix[i + 1] = prefix[i] + ss::chunk_count(d.n_rays, it.hf.nx, it.hf.ny, chunk, tile_w);
+    }
+    unsigned long long* counter;
+    ss::BatchItemDesc* ditems;
+    int64_t* dprefix;
+    ss::batch_layout(ws, n, &counter, &ditems, &dprefix);
+    B.args.items = ditems;
+    B.args.chunk_prefix = dprefix;
+    B.args.counter = counter;
+    B.args.total_chunks = prefix[n];
+    B.args.n_items = n;
+    B.args.chunk_rays = chunk;
+    B.args.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
+    B.args.refill_min = params->refill_min > 0 ? params->refill_min : 8;
+    return SS_OK;
+}
+
+// queue reset + mipmap builds + persistent kernel, all on stream s
+cudaError_t batch_enqueue(const BatchPrep& B, const ss_batch_item* items, int32_t n,
+                          cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(B.args.counter, 0, sizeof(unsigned long long), s);
+    for (int32_t i = 0; e == cudaSuccess && i < n; ++i)
+        e = ss::launch_build_maxmip(items[i].hf.h, items[i].hf.nx, items[i].hf.ny,
+                                    items[i].hf.pitch, items[i].mip, B.layouts[i], s);
+    if (e == cudaSuccess) e = ss::launch_batch_forward(B.args, B.block, B.count, s);
+    return e;
+}
+
 }  // namespace
+
+struct ss_batch_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 
 extern "C" {
 
@@ -294,6 +391,72 @@ ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, cons
     int block = params->block_threads ? params->block_threads : 256;
     cudaError_t ce = ss::launch_backward(a, block, (cudaStream_t)stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "ss_shadow_backward");
+    return SS_OK;
+}
+
+size_t ss_batch_workspace_bytes(int32_t n_items) {
+    if (n_items < 1 || n_items > (1 << 20)) return 0;
+    return ss::batch_workspace_bytes(n_items);
+}
+
+ss_status ss_batch_submit(const ss_batch_item* items, int32_t n_items, const ss_params* params,
+                          void* workspace, size_t workspace_bytes, ss_stream_t stream) {
+    BatchPrep B;
+    ss_status st = batch_prepare(items, n_items, params, workspace, workspace_bytes, B);
+    if (st != SS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // pageable source: the call returns once the image has been staged
+    cudaError_t e = cudaMemcpyAsync(static_cast<unsigned char*>(workspace) + ss::kBatchHeader,
+                                    B.image.data(), B.image.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = batch_enqueue(B, items, n_items, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_batch_submit");
+    return SS_OK;
+}
+
+ss_status ss_batch_plan_create(const ss_batch_item* items, int32_t n_items,
+                               const ss_params* params, void* workspace, size_t workspace_bytes,
+                               ss_batch_plan** plan) {
+    if (!plan) return SS_ERR_INVALID_ARG;
+    *plan = nullptr;
+    BatchPrep B;
+    ss_status st = batch_prepare(items, n_items, params, workspace, workspace_bytes, B);
+    if (st != SS_OK) return st;
+    cudaError_t e = cudaMemcpy(static_cast<unsigned char*>(workspace) + ss::kBatchHeader,
+                               B.image.data(), B.image.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_batch_plan_create (upload)");
+    cudaStream_t cs;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "ss_batch_plan_create (stream)");
+    ss_batch_plan* p = new ss_batch_plan();
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = batch_enqueue(B, items, n_items, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+        e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (p->graph) cudaGraphDestroy(p->graph);
+        delete p;
+        return cuda_fail(e, "ss_batch_plan_create (capture)");
+    }
+    *plan = p;
+    return SS_OK;
+}
+
+ss_status ss_batch_plan_launch(ss_batch_plan* plan, ss_stream_t stream) {
+    if (!plan || !plan->exec) return SS_ERR_INVALID_ARG;
+    cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_batch_plan_launch");
+    return SS_OK;
+}
+
+ss_status ss_batch_plan_destroy(ss_batch_plan* plan) {
+    if (!plan) return SS_ERR_INVALID_ARG;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
     return SS_OK;
 }
 

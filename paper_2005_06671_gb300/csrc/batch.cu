@@ -1,0 +1,203 @@
+// Batched forward: many (heightfield tile, sun) instances of uneven sizes in one
+// persistent launch with a device-side work queue.
+//
+// The instances' rays are cut into chunks (32 * rays_per_thread rays, or
+// rectangles of them); chunks of one instance are consecutive in the queue.
+// A grid of resident blocks (occupancy x SMs) pulls chunks with one global
+// atomicAdd per chunk and per warp; each warp keeps a copy of its current
+// instance's descriptor in shared memory and walks each ray with the same
+// exact descent as the single-tile forward (walk_step), refilling idle lanes
+// from its chunk.  A warp switches instance only once all its lanes are idle,
+// so lanes never mix instances.  No device-side wait: the queue is a counter.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "ss_batch.h"
+#include "ss_walk.cuh"
+
+namespace ss {
+
+// Minimum resident 256-thread blocks per SM of the batched kernel (it carries
+// queue state on top of the walk: 80 registers at 3 blocks).
+#ifndef SS_BATCH_MIN_BLOCKS
+#define SS_BATCH_MIN_BLOCKS 3
+#endif
+
+namespace {
+
+// upper_bound over the chunk prefix sums: instance that owns chunk q
+__device__ __forceinline__ int32_t owner(const int64_t* prefix, int32_t n, int64_t q) {
+    int32_t lo = 0, hi = n;   // prefix[lo] <= q < prefix[hi]
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= q) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void load_desc(BatchItemDesc* dst, const BatchItemDesc* src) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    constexpr int kWords = sizeof(BatchItemDesc) / 4;
+    for (int i = lane; i < kWords; i += 32) d[i] = __ldg(s + i);
+    __syncwarp();
+}
+
+// Warp-uniform scheduling state, kept in shared memory next to the warp's
+// instance descriptor so the lanes' registers hold only the walk.
+struct WarpSched {
+    ChunkRange C;       // current chunk of `cur`
+    int64_t stash;      // a grabbed chunk of another instance, or -1
+    int32_t c_next;     // next undrawn ray of C
+    int32_t cur;        // instance of this warp, or -1
+    int32_t open;       // the queue may still have chunks
+    float span;         // height span of `cur`
+};
+
+template <bool kCount>
+__global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(const BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    BatchItemDesc& D = reinterpret_cast<BatchItemDesc*>(smem)[wid];
+    WarpSched& S = reinterpret_cast<WarpSched*>(
+        smem + (size_t)(blockDim.x >> 5) * sizeof(BatchItemDesc))[wid];
+    const Rays grid_rays = { 0, 0, nullptr, nullptr };
+    if (lane == 0) {
+        S.C.cnt = 0;
+        S.stash = -1;
+        S.c_next = 0;
+        S.cur = -1;
+        S.open = 1;
+        S.span = 0.0f;
+    }
+    __syncwarp();
+
+    int32_t r = -1;              // index of this lane's ray within S.C, or -1
+    bool done = false;
+    RayF rf;
+    Walk w;
+    walk_begin(w);
+    while (true) {
+        unsigned act = __ballot_sync(kFull, r >= 0 && !done);
+        if (act == 0 || (S.open && S.stash < 0 && __popc(~act) >= a.refill_min)) {
+            if (done) {
+                finish_ray(D.T, grid_rays, D.O, chunk_ray(S.C, D.T.nx, r), w.best, w.bestj, w.nb,
+                           w.nl);
+                r = -1;
+                done = false;
+            }
+            // draw rays for idle lanes, taking chunks from the queue as needed
+            while (true) {
+                const unsigned idle = __ballot_sync(kFull, r < 0);
+                if (idle == 0) break;
+                const int32_t c_next = S.c_next, cnt = S.C.cnt;
+                if (c_next < cnt) {
+                    const int32_t my = c_next + __popc(idle & lanemask_lt());
+                    if (r < 0 && my < cnt) {
+                        r = my;
+                        const int64_t ray = chunk_ray(S.C, D.T.nx, r);
+                        setup_ray<true>(D.T, grid_rays, ray, S.span, rf);
+                        walk_begin(w);
+                        if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
+                            finish_ray(D.T, grid_rays, D.O, ray, w.best, w.bestj, 0, 0);
+                            r = -1;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) S.c_next = min(c_next + __popc(idle), cnt);
+                    __syncwarp();
+                    continue;
+                }
+                // current chunk exhausted: take the stashed or the next chunk
+                int64_t q = S.stash;
+                if (q < 0) {
+                    if (!S.open) break;
+                    long long got = 0;
+                    if (lane == 0) got = (long long)atomicAdd(a.counter, 1ULL);
+                    q = (int64_t)__shfl_sync(kFull, got, 0);
+                    if (q >= a.total_chunks) {
+                        __syncwarp();
+                        if (lane == 0) S.open = 0;
+                        __syncwarp();
+                        break;
+                    }
+                }
+                const int32_t item = owner(a.chunk_prefix, a.n_items, q);
+                if (item != S.cur) {
+                    const bool walking = __ballot_sync(kFull, r >= 0) != 0;
+                    __syncwarp();
+                    if (walking) {   // lanes still walk the current instance
+                        if (lane == 0) S.stash = q;
+                        __syncwarp();
+                        break;
+                    }
+                    load_desc(&D, a.items + item);
+                    if (lane == 0) {
+                        S.cur = item;
+                        S.span = __ldg(D.stats) - __ldg(D.stats + 1);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    S.stash = -1;
+                    S.C = chunk_range(q - __ldg(a.chunk_prefix + item), D.n_rays, D.T.nx, D.T.ny,
+                                      a.chunk_rays, D.tile_w);
+                    S.c_next = 0;
+                }
+                __syncwarp();
+            }
+            act = __ballot_sync(kFull, r >= 0 && !done);
+            if (act == 0) {
+                if (!S.open && S.stash < 0) break;
+                continue;
+            }
+        }
+        if (r < 0 || done) continue;
+        done = D.poly ? walk_step<kCount, true, true>(D.T, D.L, D.levels, a.kleaf, rf, w)
+                      : walk_step<kCount, true, false>(D.T, D.L, D.levels, a.kleaf, rf, w);
+    }
+}
+
+template <typename K>
+int resident_blocks(K kernel, int block, size_t smem) {
+    int per_sm = 0, dev = 0, sms = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    return per_sm * sms;
+}
+
+}  // namespace
+
+size_t batch_workspace_bytes(int32_t n_items) {
+    return kBatchHeader + align256((size_t)n_items * sizeof(BatchItemDesc)) +
+           align256((size_t)(n_items + 1) * sizeof(int64_t));
+}
+
+void batch_layout(void* ws, int32_t n_items, unsigned long long** counter, BatchItemDesc** items,
+                  int64_t** prefix) {
+    unsigned char* b = static_cast<unsigned char*>(ws);
+    *counter = reinterpret_cast<unsigned long long*>(b);
+    *items = reinterpret_cast<BatchItemDesc*>(b + kBatchHeader);
+    *prefix = reinterpret_cast<int64_t*>(b + kBatchHeader +
+                                         align256((size_t)n_items * sizeof(BatchItemDesc)));
+}
+
+cudaError_t launch_batch_forward(const BatchArgs& a, int block, bool count, cudaStream_t s) {
+    const size_t smem = (size_t)(block / 32) * (sizeof(BatchItemDesc) + sizeof(WarpSched));
+    if (count) {
+        const int grid = resident_blocks(batch_dp_kernel<true>, block, smem);
+        batch_dp_kernel<true><<<grid, block, smem, s>>>(a);
+    } else {
+        const int grid = resident_blocks(batch_dp_kernel<false>, block, smem);
+        batch_dp_kernel<false><<<grid, block, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ss

@@ -9,89 +9,9 @@
 #include <stdint.h>
 
 #include "ss_launch.h"
+#include "ss_walk.cuh"
 
 namespace ss {
-
-__device__ __forceinline__ int64_t ray_count(const Tile& T, const Rays& R) {
-    return R.mode == 0 ? (int64_t)T.nx * T.ny : R.n;
-}
-
-// cos(eps_p) of ray r's origin in float32 (relative error ~1e-7), enough to
-// decide whether its light is saturated.
-__device__ __forceinline__ float cos_elev_f32(const FwdArgs& a, int64_t r) {
-    float u, v;
-    if (a.R.mode == 0) {
-        const int64_t vv = r / a.T.nx;
-        u = (float)(r - vv * a.T.nx);
-        v = (float)vv;
-    } else {
-        u = a.R.uv[2 * r];
-        v = a.R.uv[2 * r + 1];
-    }
-    const float g = (float)a.T.g, R = (float)a.T.R;
-    const float X = (u - (float)a.T.cx) * g, Y = (v - (float)a.T.cy) * g;
-    const float se = (X * (float)a.T.sx + Y * (float)a.T.sy + R * (float)a.T.sz) *
-                     rsqrtf(X * X + Y * Y + R * R);
-    return sqrtf(fmaxf(0.0f, 1.0f - se * se));
-}
-
-// Final value of one ray: re-evaluate the argmin sample in FP64 unless the
-// light is certainly saturated (|c*| cos(eps) >= 1.001 alpha), then the
-// disc-occlusion formula (Eq. discfrac).
-__device__ __forceinline__ void finish_ray(const FwdArgs& a, int64_t r, float best,
-                                           int32_t bestj, int32_t nb, int32_t nl) {
-    float light, cost;
-    if (bestj < 0) {
-        light = 1.0f;
-        cost = INFINITY;
-    } else if (fabsf(best) * cos_elev_f32(a, r) >= 1.001f * a.T.alpha_f) {
-        light = best > 0.0f ? 1.0f : 0.0f;
-        cost = best;
-    } else {
-        double up, vp, hp, href, ow[4];
-        int32_t oi0, oj0;
-        ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
-        Geom64 G;
-        geom64(a.T, up, vp, hp, G);
-        double c = leaf_cost64(a.T, G, bestj);
-        light = (float)disc_light64(c * G.cos_e / a.T.alpha);
-        cost = (float)c;
-    }
-    a.O.light[r] = light;
-    a.O.argmin[r] = bestj;
-    if (a.O.cost) a.O.cost[r] = cost;
-    if (a.O.counters) {
-        a.O.counters[2 * r] = nb;
-        a.O.counters[2 * r + 1] = nl;
-    }
-}
-
-template <bool kGrid>
-__device__ __forceinline__ void setup_ray(const FwdArgs& a, int64_t r, float span, RayF& rf) {
-    double up, vp, hp, href;
-    if (kGrid) {
-        const int64_t v = r / a.T.nx, u = r - v * a.T.nx;
-        up = (double)u;
-        vp = (double)v;
-        hp = href = (double)a.T.h[v * a.T.pitch + u];
-    } else {
-        double ow[4];
-        int32_t oi0, oj0;
-        ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
-    }
-    Geom64 G;
-    geom64(a.T, up, vp, hp, G);
-    make_rayf(a.T, G, href, span, rf);
-    if (kGrid) rf.X = 0.0f;
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-constexpr unsigned kFull = 0xffffffffu;
 
 // Minimum resident 256-thread blocks per SM for the forward kernels (caps
 // registers at 65536 / (256 * SS_FWD_MIN_BLOCKS)).
@@ -106,23 +26,14 @@ constexpr unsigned kFull = 0xffffffffu;
 // refill_min lanes of the warp are waiting (or all are), the warp services
 // them together: finished rays are written, and the waiting lanes draw the
 // next rays of the block pool (one shared-memory atomic per warp).
-struct BlockPool {
-    int64_t lo;
-    int32_t cnt;
-};
-
-__device__ __forceinline__ BlockPool block_pool(const FwdArgs& a, int32_t* s_next) {
+__device__ __forceinline__ ChunkRange block_pool(const FwdArgs& a, int32_t* s_next) {
     if (threadIdx.x == 0) *s_next = 0;
-    BlockPool P;
-    const int64_t n = ray_count(a.T, a.R);
-    P.lo = (int64_t)blockIdx.x * a.rays_per_block;
-    const int64_t c = n - P.lo;
-    P.cnt = (int32_t)(c < a.rays_per_block ? c : a.rays_per_block);
-    return P;
+    return chunk_range(blockIdx.x, ray_count(a.T, a.R), a.T.nx, a.T.ny, (int32_t)a.rays_per_block,
+                       a.R.mode == 0 ? a.tile_w : 0);
 }
 
 // Draw rays for this warp's lanes with r < 0; returns the new local index or -1.
-__device__ __forceinline__ int32_t draw(const BlockPool& P, int32_t* s_next, int32_t r,
+__device__ __forceinline__ int32_t draw(const ChunkRange& P, int32_t* s_next, int32_t r,
                                         bool& open) {
     const unsigned idle = __ballot_sync(kFull, r < 0);
     const int nidle = __popc(idle);
@@ -136,16 +47,8 @@ __device__ __forceinline__ int32_t draw(const BlockPool& P, int32_t* s_next, int
 }
 
 // ---------------------------------------------------------------- descent
-// Stackless depth-first walk over aligned sample blocks [s0+1, s0+2^k]:
-// a block's bound (probe) is compared with the running minimum; blocks that
-// cannot win are skipped, the others split; blocks of <= 2^kleaf samples are
-// evaluated sample by sample.  After a block, the walk continues at
-// s0 += 2^k with k = ctz(s0), the next block in near-to-far order, so samples
-// are evaluated in increasing j and a strict '<' keeps the smallest j among
-// equal costs.  Each loop iteration is exactly one probe per walking lane.
-// Blocks are aligned to their size, so for k = ctz(s0) the block may end past
-// j_hi; it is clipped.  The leaf level bounds the smallest block that gets a
-// bound probe: runs of 2^(kleaf+1) samples are evaluated directly.
+// Each loop iteration is one probe of the exact descent (walk_step) per
+// walking lane.
 template <bool kCount, bool kGrid, bool kPoly>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(const FwdArgs a) {
     __shared__ LevelTab s_lev;
@@ -154,7 +57,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
         s_lev.ptr[threadIdx.x] = a.P.ptr[threadIdx.x];
         s_lev.pitch[threadIdx.x] = (uint32_t)a.P.pitch[threadIdx.x];
     }
-    const BlockPool P = block_pool(a, &s_next);
+    const ChunkRange P = block_pool(a, &s_next);
     __syncthreads();
     const float span = a.stats[0] - a.stats[1];
     const int32_t kleaf = a.kleaf, levels = a.P.levels;
@@ -162,13 +65,13 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
     int32_t r = -1;
     bool done = false, open = true;
     RayF rf;
-    float best = INFINITY;
-    int32_t bestj = -1, nb = 0, nl = 0, s0 = 0, k = 0;
+    Walk w;
+    walk_begin(w);
     while (true) {
         unsigned act = __ballot_sync(kFull, r >= 0 && !done);
         if (act == 0 || (open && __popc(~act) >= a.refill_min)) {
             if (done) {
-                finish_ray(a, P.lo + r, best, bestj, nb, nl);
+                finish_ray(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj, w.nb, w.nl);
                 r = -1;
                 done = false;
             }
@@ -176,16 +79,10 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
                 const int32_t nr = draw(P, &s_next, r, open);
                 if (nr >= 0 && r < 0) {
                     r = nr;
-                    setup_ray<kGrid>(a, P.lo + r, span, rf);
-                    best = INFINITY;
-                    bestj = -1;
-                    nb = nl = s0 = 0;
-                    // While best is +inf every block on the left spine is split
-                    // without a bound being able to prune it, so the walk starts
-                    // directly with the first run of leaves (same order, same result).
-                    k = 0;
+                    setup_ray<kGrid>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
+                    walk_begin(w);
                     if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
-                        finish_ray(a, P.lo + r, best, bestj, 0, 0);
+                        finish_ray(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj, 0, 0);
                         r = -1;
                     }
                 }
@@ -197,27 +94,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
             }
         }
         if (r < 0 || done) continue;
-        const bool leaf = (k == 0);
-        const int32_t s1 = s0 + 1;
-        int32_t ja = leaf ? s1 : max(s1, rf.j_lo);
-        int32_t jb = leaf ? s1 : min(s0 + (1 << k), rf.j_hi);
-        const bool valid = leaf ? (s1 >= rf.j_lo) : (ja <= jb);
-        ja = valid ? ja : rf.j_lo;
-        jb = valid ? jb : rf.j_lo;
-        const float v = probe<kGrid, kPoly>(a.T, s_lev, levels, rf, ja, jb, leaf);
-        const bool improve = valid && leaf && (v < best);
-        best = improve ? v : best;
-        bestj = improve ? ja : bestj;
-        const bool descend = valid && !leaf && !(v > best);
-        if (kCount) {
-            nl += (valid && leaf) ? 1 : 0;
-            nb += (valid && !leaf) ? 1 : 0;
-        }
-        const int32_t s_adv = s0 + (1 << k);
-        const int32_t k_adv = __ffs(s_adv) - 1;
-        s0 = descend ? s0 : s_adv;
-        k = descend ? ((k - 1 > kleaf) ? k - 1 : 0) : ((k_adv <= kleaf) ? 0 : k_adv);
-        done = !descend && (s_adv >= rf.j_hi);
+        done = walk_step<kCount, kGrid, kPoly>(a.T, s_lev, levels, kleaf, rf, w);
     }
 }
 
@@ -230,7 +107,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
 template <bool kCount, bool kGrid, bool kPoly>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel(const FwdArgs a) {
     __shared__ int32_t s_next;
-    const BlockPool P = block_pool(a, &s_next);
+    const ChunkRange P = block_pool(a, &s_next);
     __syncthreads();
     const float hmax = a.stats[0];
     const float span = a.stats[0] - a.stats[1];
@@ -246,7 +123,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel
         unsigned act = __ballot_sync(kFull, r >= 0 && !done);
         if (act == 0 || (open && __popc(~act) >= a.refill_min)) {
             if (done) {
-                finish_ray(a, P.lo + r, best, bestj, 0, nl);
+                finish_ray(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), best, bestj, 0, nl);
                 r = -1;
                 done = false;
             }
@@ -254,7 +131,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel
                 const int32_t nr = draw(P, &s_next, r, open);
                 if (nr >= 0 && r < 0) {
                     r = nr;
-                    setup_ray<kGrid>(a, P.lo + r, span, rf);
+                    setup_ray<kGrid>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
                     best = INFINITY;
                     bestj = -1;
                     nl = 0;
@@ -266,7 +143,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel
                                            0.5f * rf.B * rf.B * rf.inv_2rho);
                     G = 3.0f * kGuardRel * (rf.guard0 + fabsf(hmax_rel) + rb);
                     if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
-                        finish_ray(a, P.lo + r, best, bestj, 0, 0);
+                        finish_ray(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), best, bestj, 0, 0);
                         r = -1;
                     }
                 }
@@ -413,8 +290,9 @@ static int resident_grid(K kernel, int block, int64_t n_threads) {
 }
 
 static int pool_grid(const FwdArgs& a) {
-    int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
-    return (int)((n + a.rays_per_block - 1) / a.rays_per_block);
+    const int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
+    return (int)chunk_count(n, a.T.nx, a.T.ny, (int32_t)a.rays_per_block,
+                            a.R.mode == 0 ? a.tile_w : 0);
 }
 
 template <template <bool, bool, bool> class Launch>

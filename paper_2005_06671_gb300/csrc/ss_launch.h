@@ -32,6 +32,7 @@ struct FwdArgs {
     int64_t rays_per_block;   // rays owned by one block
     int32_t refill_min;       // waiting lanes that trigger a warp service
     int32_t poly;             // 1: the rise series is valid for every ray
+    int32_t tile_w;           // grid mode: ray-rectangle width (0 = row-major runs)
 };
 
 struct BwdArgs {

@@ -1,0 +1,192 @@
+// Per-ray pieces shared by the single-tile and batched forward kernels:
+// setup of a ray's float32 state, one step of the exact descent, and the
+// final write of a ray's outputs.
+#pragma once
+
+#include "ss_device.cuh"
+
+namespace ss {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int64_t ray_count(const Tile& T, const Rays& R) {
+    return R.mode == 0 ? (int64_t)T.nx * T.ny : R.n;
+}
+
+// cos(eps_p) of ray r's origin in float32 (relative error ~1e-7), enough to
+// decide whether its light is saturated.
+__device__ __forceinline__ float cos_elev_f32(const Tile& T, const Rays& R, int64_t r) {
+    float u, v;
+    if (R.mode == 0) {
+        const int64_t vv = r / T.nx;
+        u = (float)(r - vv * T.nx);
+        v = (float)vv;
+    } else {
+        u = R.uv[2 * r];
+        v = R.uv[2 * r + 1];
+    }
+    const float g = (float)T.g, Rs = (float)T.R;
+    const float X = (u - (float)T.cx) * g, Y = (v - (float)T.cy) * g;
+    const float se = (X * (float)T.sx + Y * (float)T.sy + Rs * (float)T.sz) *
+                     rsqrtf(X * X + Y * Y + Rs * Rs);
+    return sqrtf(fmaxf(0.0f, 1.0f - se * se));
+}
+
+// Final value of one ray: re-evaluate the argmin sample in FP64 unless the
+// light is certainly saturated (|c*| cos(eps) >= 1.001 alpha), then the
+// disc-occlusion formula (Eq. discfrac).
+__device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const Outputs& O,
+                                           int64_t r, float best, int32_t bestj, int32_t nb,
+                                           int32_t nl) {
+    float light, cost;
+    if (bestj < 0) {
+        light = 1.0f;
+        cost = INFINITY;
+    } else if (fabsf(best) * cos_elev_f32(T, R, r) >= 1.001f * T.alpha_f) {
+        light = best > 0.0f ? 1.0f : 0.0f;
+        cost = best;
+    } else {
+        double up, vp, hp, href, ow[4];
+        int32_t oi0, oj0;
+        ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
+        Geom64 G;
+        geom64(T, up, vp, hp, G);
+        double c = leaf_cost64(T, G, bestj);
+        light = (float)disc_light64(c * G.cos_e / T.alpha);
+        cost = (float)c;
+    }
+    O.light[r] = light;
+    O.argmin[r] = bestj;
+    if (O.cost) O.cost[r] = cost;
+    if (O.counters) {
+        O.counters[2 * r] = nb;
+        O.counters[2 * r + 1] = nl;
+    }
+}
+
+template <bool kGrid>
+__device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t r, float span,
+                                          RayF& rf) {
+    double up, vp, hp, href;
+    if (kGrid) {
+        const int64_t v = r / T.nx, u = r - v * T.nx;
+        up = (double)u;
+        vp = (double)v;
+        hp = href = (double)T.h[v * T.pitch + u];
+    } else {
+        double ow[4];
+        int32_t oi0, oj0;
+        ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
+    }
+    Geom64 G;
+    geom64(T, up, vp, hp, G);
+    make_rayf(T, G, href, span, rf);
+    if (kGrid) rf.X = 0.0f;
+}
+
+
+
+
+// Grid-mode rays grouped into chunks of `chunk` rays: with tile_w == 0 the
+// chunks are runs of consecutive ray ids (row-major texels); with tile_w > 0
+// (chunk a multiple of tile_w) they are tile_w x (chunk / tile_w) rectangles
+// of texels in row-major order of rectangles, smaller at the right and bottom
+// edges.  A chunk's rays are drawn in row-major order within it.
+struct ChunkRange {
+    int64_t lo;       // first ray id (linear chunks)
+    int32_t cnt;      // rays in the chunk
+    int32_t x0, y0, w;   // rectangle origin and width (rectangular chunks)
+    int32_t rect;
+};
+
+__host__ __device__ __forceinline__ int64_t chunk_count(int64_t n, int32_t nx, int32_t ny,
+                                                        int32_t chunk, int32_t tile_w) {
+    if (tile_w <= 0) return (n + chunk - 1) / chunk;
+    const int32_t th = chunk / tile_w;
+    return (int64_t)((nx + tile_w - 1) / tile_w) * ((ny + th - 1) / th);
+}
+
+__device__ __forceinline__ ChunkRange chunk_range(int64_t c, int64_t n, int32_t nx, int32_t ny,
+                                                  int32_t chunk, int32_t tile_w) {
+    ChunkRange C;
+    if (tile_w <= 0) {
+        C.rect = 0;
+        C.lo = c * chunk;
+        const int64_t left = n - C.lo;
+        C.cnt = (int32_t)(left < chunk ? left : chunk);
+        C.x0 = C.y0 = C.w = 0;
+    } else {
+        const int32_t th = chunk / tile_w, rx = (nx + tile_w - 1) / tile_w;
+        const int32_t bx = (int32_t)(c % rx), by = (int32_t)(c / rx);
+        C.rect = 1;
+        C.lo = 0;
+        C.x0 = bx * tile_w;
+        C.y0 = by * th;
+        C.w = min(tile_w, nx - C.x0);
+        C.cnt = C.w * min(th, ny - C.y0);
+    }
+    return C;
+}
+
+__device__ __forceinline__ int64_t chunk_ray(const ChunkRange& C, int32_t nx, int32_t i) {
+    if (!C.rect) return C.lo + i;
+    const int32_t q = i / C.w;
+    return (int64_t)(C.y0 + q) * nx + C.x0 + (i - q * C.w);
+}
+
+// Lane state of the descent over one ray.
+struct Walk {
+    float best;
+    int32_t bestj, s0, k, nb, nl;
+};
+
+// While best is +inf every block on the left spine of the tree is split without
+// a bound being able to prune it, so the walk starts directly with the first
+// run of leaves (same order, same result).
+__device__ __forceinline__ void walk_begin(Walk& w) {
+    w.best = INFINITY;
+    w.bestj = -1;
+    w.s0 = w.k = w.nb = w.nl = 0;
+}
+
+// One probe of the exact descent and the state update; true when finished.
+// Stackless depth-first walk over aligned sample blocks [s0+1, s0+2^k]: a
+// block's bound is compared with the running minimum; blocks that cannot win
+// are skipped, the others split; blocks of <= 2^kleaf samples are evaluated
+// sample by sample.  After a block the walk continues at s0 += 2^k with
+// k = ctz(s0), the next block in near-to-far order, so samples are evaluated
+// in increasing j and a strict '<' keeps the smallest j among equal costs.
+// Blocks are clipped to [j_lo, j_hi].
+template <bool kCount, bool kGrid, bool kPoly>
+__device__ __forceinline__ bool walk_step(const Tile& T, const LevelTab& L, int32_t levels,
+                                          int32_t kleaf, const RayF& rf, Walk& w) {
+    const bool leaf = (w.k == 0);
+    const int32_t s1 = w.s0 + 1;
+    int32_t ja = leaf ? s1 : max(s1, rf.j_lo);
+    int32_t jb = leaf ? s1 : min(w.s0 + (1 << w.k), rf.j_hi);
+    const bool valid = leaf ? (s1 >= rf.j_lo) : (ja <= jb);
+    ja = valid ? ja : rf.j_lo;
+    jb = valid ? jb : rf.j_lo;
+    const float v = probe<kGrid, kPoly>(T, L, levels, rf, ja, jb, leaf);
+    const bool improve = valid && leaf && (v < w.best);
+    w.best = improve ? v : w.best;
+    w.bestj = improve ? ja : w.bestj;
+    const bool descend = valid && !leaf && !(v > w.best);
+    if (kCount) {
+        w.nl += (valid && leaf) ? 1 : 0;
+        w.nb += (valid && !leaf) ? 1 : 0;
+    }
+    const int32_t s_adv = w.s0 + (1 << w.k);
+    const int32_t k_adv = __ffs(s_adv) - 1;
+    w.s0 = descend ? w.s0 : s_adv;
+    w.k = descend ? ((w.k - 1 > kleaf) ? w.k - 1 : 0) : ((k_adv <= kleaf) ? 0 : k_adv);
+    return !descend && (s_adv >= rf.j_hi);
+}
+
+}  // namespace ss

@@ -106,9 +106,9 @@ def ss_build_maxmip(hf: Heightfield, mip=None, stream=None):
 
 # ----------------------------------------------------------------- forward
 def _params(max_len_m, step_texels, flags, block_threads, leaf_level, rays_per_thread=0,
-            refill_min=0):
+            refill_min=0, ray_tile_w=0):
     return SSParams(float(max_len_m), float(step_texels), int(flags), int(block_threads),
-                    int(leaf_level), int(rays_per_thread), int(refill_min), 0)
+                    int(leaf_level), int(rays_per_thread), int(refill_min), int(ray_tile_w), 0)
 
 
 def _rays(hf, uv, lift):
@@ -144,12 +144,12 @@ def _outputs(n, device, want_cost, count, out):
 
 
 def _forward(fn_name, hf, mip, sun, max_len_m, step_texels, uv, lift, flags, block_threads,
-             leaf_level, want_cost, out, stream, rays_per_thread=0, refill_min=0):
+             leaf_level, want_cost, out, stream, rays_per_thread=0, refill_min=0, ray_tile_w=0):
     rays, n = _rays(hf, uv, lift)
     count = bool(flags & SS_FLAG_COUNT_SAMPLES)
     oc, res = _outputs(n, hf.h.device, want_cost, count, out)
     prm = _params(max_len_m, step_texels, flags, block_threads, leaf_level, rays_per_thread,
-                  refill_min)
+                  refill_min, ray_tile_w)
     fn = getattr(_abi.lib(), fn_name)
     check(fn(ctypes.byref(hf.c()), _ptr(mip), ctypes.byref(rays), ctypes.byref(sun.c()),
              ctypes.byref(prm), ctypes.byref(oc), _stream_ptr(stream)), fn_name)
@@ -158,21 +158,24 @@ def _forward(fn_name, hf, mip, sun, max_len_m, step_texels, uv, lift, flags, blo
 
 def ss_shadow_forward(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
                       lift=None, count_samples=False, block_threads=0, leaf_level=-1,
-                      want_cost=True, out=None, stream=None, rays_per_thread=0, refill_min=0):
+                      want_cost=True, out=None, stream=None, rays_per_thread=0, refill_min=0,
+                      ray_tile_w=0):
     """Exact max-mip descent.  Returns dict(light, argmin, cost, counters)."""
     flags = SS_FLAG_COUNT_SAMPLES if count_samples else 0
     return _forward("ss_shadow_forward", hf, mip, sun, max_len_m, step_texels, uv, lift, flags,
                     block_threads, leaf_level, want_cost, out, stream, rays_per_thread,
-                    refill_min)
+                    refill_min, ray_tile_w)
 
 
 def ss_shadow_uniform(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
                       lift=None, count_samples=False, early_exit=True, block_threads=0,
-                      want_cost=True, out=None, stream=None, rays_per_thread=0, refill_min=0):
+                      want_cost=True, out=None, stream=None, rays_per_thread=0, refill_min=0,
+                      ray_tile_w=0):
     """Uniform stepping over every sample (exact early exit unless disabled)."""
     flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (0 if early_exit else SS_FLAG_NO_EARLY_EXIT)
     return _forward("ss_shadow_uniform", hf, mip, sun, max_len_m, step_texels, uv, lift, flags,
-                    block_threads, -1, want_cost, out, stream, rays_per_thread, refill_min)
+                    block_threads, -1, want_cost, out, stream, rays_per_thread, refill_min,
+                    ray_tile_w)
 
 
 # ---------------------------------------------------------------- backward
@@ -235,3 +238,85 @@ class ShadowFn(torch.autograd.Function):
 
 def shadow(h, sun_angles, texel_m, radius_m, alpha, max_len_m, step_texels=0.5):
     return ShadowFn.apply(h, sun_angles, texel_m, radius_m, alpha, max_len_m, step_texels)
+
+
+# ----------------------------------------------------------------- batched
+class Batch:
+    """Inputs and outputs of one batch: grid-mode rays on gnomonic tiles.
+
+    ``hfs``: list of Heightfield; ``suns``: list of Sun (one per tile).  Allocates
+    the mipmap buffers, per-ray outputs and the device workspace once; they are
+    reused by every submit/plan launch of this batch.
+    """
+
+    def __init__(self, hfs, suns, max_len_m, step_texels=0.5, count_samples=False,
+                 want_cost=False, block_threads=0, leaf_level=-1, rays_per_thread=0,
+                 refill_min=0, ray_tile_w=0):
+        if len(hfs) != len(suns) or not hfs:
+            raise ValueError("need one sun per heightfield, at least one item")
+        self.hfs, self.suns = list(hfs), list(suns)
+        dev = hfs[0].h.device
+        flags = SS_FLAG_COUNT_SAMPLES if count_samples else 0
+        self.params = SSParams(float(max_len_m), float(step_texels), int(flags), int(block_threads),
+                               int(leaf_level), int(rays_per_thread), int(refill_min),
+                               int(ray_tile_w), 0)
+        n = len(hfs)
+        self.items = (_abi.SSBatchItem * n)()
+        self.mips, self.outs = [], []
+        for i, (hf, sun) in enumerate(zip(hfs, suns)):
+            ny, nx = hf.shape
+            mip = torch.empty(maxmip_bytes(nx, ny) // 4, dtype=torch.float32, device=dev)
+            oc, res = _outputs(nx * ny, dev, want_cost, count_samples, None)
+            self.items[i].hf = hf.c()
+            self.items[i].mip = mip.data_ptr()
+            self.items[i].sun = sun.c()
+            self.items[i].out = oc
+            self.mips.append(mip)
+            self.outs.append(res)
+        nb = int(_abi.lib().ss_batch_workspace_bytes(n))
+        self.workspace = torch.empty(nb, dtype=torch.uint8, device=dev)
+        self._plan = None
+
+    def submit(self, stream=None):
+        check(_abi.lib().ss_batch_submit(ctypes.cast(self.items, ctypes.c_void_p), len(self.hfs),
+                                         ctypes.byref(self.params), _ptr(self.workspace),
+                                         self.workspace.numel(), _stream_ptr(stream)),
+              "ss_batch_submit")
+        return self.outs
+
+    def plan(self):
+        """Capture the batch into a CUDA graph (uploads descriptors synchronously)."""
+        if self._plan is None:
+            h = ctypes.c_void_p()
+            check(_abi.lib().ss_batch_plan_create(ctypes.cast(self.items, ctypes.c_void_p),
+                                                  len(self.hfs), ctypes.byref(self.params),
+                                                  _ptr(self.workspace), self.workspace.numel(),
+                                                  ctypes.byref(h)), "ss_batch_plan_create")
+            self._plan = h
+        return self
+
+    def launch(self, stream=None):
+        """Replay the captured graph."""
+        self.plan()
+        check(_abi.lib().ss_batch_plan_launch(self._plan, _stream_ptr(stream)),
+              "ss_batch_plan_launch")
+        return self.outs
+
+    def close(self):
+        if self._plan is not None:
+            _abi.lib().ss_batch_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ss_batch_submit(hfs, suns, max_len_m, **kw):
+    """One-shot batch: returns the per-item output dicts (light, argmin, cost, counters)."""
+    b = Batch(hfs, suns, max_len_m, **kw)
+    outs = b.submit()
+    b.close()
+    return outs

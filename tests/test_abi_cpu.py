@@ -42,7 +42,7 @@ def test_status_strings_and_layout_queries():
 def _good():
     hf = SSHeightfield(FAKE, 64, 64, 64, 10.0, 1737.4e3, 0)
     sun = SSSun(math.radians(1.0), 0.5, math.radians(0.2665))
-    prm = SSParams(1000.0, 0.5, 0, 0, -1, 0, 0, 0)
+    prm = SSParams(1000.0, 0.5, 0, 0, -1, 0, 0, 0, 0)
     rays = SSRays(0, 0, None, None)
     out = SSOutputs(FAKE, FAKE, None, None)
     return hf, sun, prm, rays, out
@@ -78,6 +78,8 @@ def _fwd(hf, sun, prm, rays, out, mip=FAKE):
     (lambda a: setattr(a[2], "rays_per_thread", -1), 1),
     (lambda a: setattr(a[2], "rays_per_thread", 5000), 1),
     (lambda a: setattr(a[2], "refill_min", 33), 1),
+    (lambda a: setattr(a[2], "ray_tile_w", -2), 1),
+    (lambda a: setattr(a[2], "ray_tile_w", 100), 1),   # must divide the block's rays
     (lambda a: setattr(a[3], "mode", 7), 1),
     (lambda a: (setattr(a[3], "mode", 1), setattr(a[3], "n", -3)), 2),
     (lambda a: (setattr(a[3], "mode", 1), setattr(a[3], "n", 5)), 1),
@@ -92,6 +94,34 @@ def test_forward_rejects_bad_arguments(mutate, expect):
     mutate(args)
     hf, sun, prm, rays, out, mip = args
     assert _fwd(hf, sun, prm, rays, out, mip) == expect
+
+
+def test_batch_entry_points_reject_bad_arguments():
+    lib = _abi.lib()
+    hf, sun, prm, rays, out = _good()
+    item = _abi.SSBatchItem(hf, FAKE, sun, out)
+    items = (_abi.SSBatchItem * 2)(item, item)
+    ws = lib.ss_batch_workspace_bytes(2)
+    assert ws > 0 and lib.ss_batch_workspace_bytes(0) == 0
+    p_items = ctypes.cast(items, ctypes.c_void_p)
+    assert lib.ss_batch_submit(None, 2, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws, None) == 1
+    assert lib.ss_batch_submit(p_items, 0, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws, None) == 2
+    assert lib.ss_batch_submit(p_items, 2, ctypes.byref(prm), None, ws, None) == 1
+    assert lib.ss_batch_submit(p_items, 2, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws - 1, None) == 3
+    items[1].hf.projection = 1
+    assert lib.ss_batch_submit(p_items, 2, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws, None) == 7
+    items[1].hf.projection = 0
+    items[1].out.light = None
+    assert lib.ss_batch_submit(p_items, 2, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws, None) == 1
+    items[1].out.light = FAKE
+    prm.rays_per_thread = 4
+    prm.ray_tile_w = 48      # 128 rays per chunk: 48 does not divide it
+    assert lib.ss_batch_submit(p_items, 2, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws, None) == 1
+    plan = ctypes.c_void_p()
+    assert lib.ss_batch_plan_create(p_items, 2, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws,
+                                    None) == 1
+    assert lib.ss_batch_plan_launch(None, None) == 1
+    assert lib.ss_batch_plan_destroy(None) == 1
 
 
 def test_other_entry_points_reject_bad_arguments():
