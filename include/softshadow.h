@@ -232,6 +232,27 @@ ss_status ss_batch_plan_create(const ss_batch_item* items, int32_t n_items,
 ss_status ss_batch_plan_launch(ss_batch_plan* plan, ss_stream_t stream);
 ss_status ss_batch_plan_destroy(ss_batch_plan* plan);
 
+/* ss_batch_submit without any device allocation (no counterpart in the paper;
+ * an interface for callers that cannot allocate).  Some callers cannot give the
+ * batch a workspace: a renderer's frame loop that must not call cudaMalloc
+ * (it may synchronise the device and stall the frame), or a host program
+ * whose device memory belongs to another allocator.  This entry point keeps
+ * the workspace in a fixed array of ss_batch_static_scratch_bytes() bytes in
+ * the library's device image instead (every GPU that loads the library holds
+ * it until the process exits) and otherwise behaves as ss_batch_submit.
+ * Limit: at most SS_BATCH_STATIC_MAX_ITEMS items; more returns SS_ERR_BAD_SIZE
+ * (message in ss_last_error_string()).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) for that device; make
+ * that first call before any stream capture.  Every call reuses the same
+ * array, overwriting the previous call's descriptors and resetting its queue
+ * counter: calls that overlap on the GPU (different streams, not ordered)
+ * race and give wrong results; order them on one stream or synchronise.
+ * Calls no cudaMalloc/cudaFree or other allocating routine. */
+#define SS_BATCH_STATIC_MAX_ITEMS 256
+size_t ss_batch_static_scratch_bytes(void);
+ss_status ss_batch_submit_static(const ss_batch_item* items, int32_t n_items,
+                                 const ss_params* params, ss_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

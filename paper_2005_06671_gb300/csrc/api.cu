@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "../../include/softshadow.h"
@@ -457,6 +458,81 @@ ss_status ss_batch_plan_destroy(ss_batch_plan* plan) {
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->graph) cudaGraphDestroy(plan->graph);
     delete plan;
+    return SS_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------- batch without any allocation
+// Some callers cannot allocate device memory for the batch workspace: a
+// renderer's per-frame loop, where cudaMalloc may synchronise the whole device
+// and stall the frame; host programs whose device memory belongs to another
+// allocator (an engine or framework pool) that third-party libraries must not
+// bypass; code that may not call allocation routines at all.  For them,
+// ss_batch_submit_static keeps its workspace in a fixed array in the library's
+// device image instead of a caller buffer.
+namespace {
+
+constexpr int32_t kStaticMaxItems = SS_BATCH_STATIC_MAX_ITEMS;
+constexpr size_t kStaticBytes =
+    ss::kBatchHeader +
+    (((size_t)kStaticMaxItems * sizeof(ss::BatchItemDesc) + 255) & ~(size_t)255) +
+    (((size_t)(kStaticMaxItems + 1) * sizeof(int64_t) + 255) & ~(size_t)255);
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_batch_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (a host-side name of a __device__ array is not a device address).
+ss_status static_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_batch_submit_static (device)");
+    if (dev < 0 || dev >= kMaxDevices) return SS_ERR_INTERNAL;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_batch_static_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "ss_batch_submit_static (symbol)");
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return SS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ss_batch_static_scratch_bytes(void) { return kStaticBytes; }
+
+ss_status ss_batch_submit_static(const ss_batch_item* items, int32_t n_items,
+                                 const ss_params* params, ss_stream_t stream) {
+    if (n_items > kStaticMaxItems) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "ss_batch_submit_static: %d items exceed the static scratch limit of %d",
+                 (int)n_items, (int)kStaticMaxItems);
+        return SS_ERR_BAD_SIZE;
+    }
+    if (!items || !params) return SS_ERR_INVALID_ARG;
+    if (n_items < 1) return SS_ERR_BAD_SIZE;
+    void* ws = nullptr;
+    ss_status st = static_scratch(&ws);
+    if (st != SS_OK) return st;
+    BatchPrep B;
+    st = batch_prepare(items, n_items, params, ws, kStaticBytes, B);
+    if (st != SS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // descriptors from the previous call are overwritten; the queue counter is
+    // reset by batch_enqueue before the kernel runs
+    cudaError_t e = cudaMemcpyAsync(static_cast<unsigned char*>(ws) + ss::kBatchHeader,
+                                    B.image.data(), B.image.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = batch_enqueue(B, items, n_items, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_batch_submit_static");
     return SS_OK;
 }
 
