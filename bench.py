@@ -47,6 +47,7 @@ def parse_args(argv=None):
     p.add_argument("--leaf-level", type=int, default=-1)
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-batched", action="store_true", help="skip the 64-instance batched leg")
     p.add_argument("--size", type=int, default=0,
                    help="profiling only: run the mid recipe at this tile size instead of 4096")
     return p.parse_args(argv)
@@ -293,8 +294,32 @@ def run_ours(args):
                       "same_results_as_descent": bool(torch.equal(ures["argmin"], res["argmin"]))}
     out["speedup_vs_uniform"] = value / uni_value
 
+    # ---- light-only mode (saturation cutoffs; exact light), both kernels
+    lo = {}
+    for name, fn in (("descent", ss.ss_shadow_forward), ("uniform", ss.ss_shadow_uniform)):
+        ms_l = []
+        for k in range(3):
+            flush.zero_()
+            e0, e1, e2 = ev[k]
+            e0.record(stream)
+            ss.ss_build_maxmip(hf, mip)
+            e1.record(stream)
+            fn(hf, mip, sun, lmax, out=bufs, want_cost=False, light_only=True)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            ms_l.append(e0.elapsed_time(e2))
+        lo[name] = statistics.mean(ms_l)
+    out["light_only"] = {"value": n_rays / (lo["descent"] / 1e3), "unit": UNIT,
+                         "ms_per_step": lo["descent"],
+                         "uniform_value": n_rays / (lo["uniform"] / 1e3),
+                         "speedup_vs_uniform": lo["uniform"] / lo["descent"],
+                         "note": "SS_FLAG_LIGHT_ONLY: same step, exact light; argmin exact "
+                                 "in the penumbra only"}
+
     # ---- forward + backward (loss gradient of ones), rays/s
     gl = torch.ones(n_rays, dtype=torch.float32, device=dev)
+    cost_buf = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    fb_bufs = dict(light=light, argmin=argmin, cost=cost_buf)
     gh = torch.zeros_like(hf.h)
     gs = torch.zeros(5, dtype=torch.float64, device=dev)
     fb_ms = []
@@ -305,9 +330,9 @@ def run_ours(args):
         e0, e1, e2 = ev[k]
         e0.record(stream)
         ss.ss_build_maxmip(hf, mip)
-        ss.ss_shadow_forward(hf, mip, sun, lmax, out=bufs, want_cost=False)
+        ss.ss_shadow_forward(hf, mip, sun, lmax, out=fb_bufs)
         e1.record(stream)
-        ss.ss_shadow_backward(hf, sun, lmax, argmin, gl, grad_h=gh, grad_sun=gs)
+        ss.ss_shadow_backward(hf, sun, lmax, argmin, gl, grad_h=gh, grad_sun=gs, cost=cost_buf)
         e2.record(stream)
         torch.cuda.synchronize()
         fb_ms.append(e0.elapsed_time(e2))
@@ -339,6 +364,10 @@ def run_ours(args):
                   "d2h_bytes_per_step": int(light_host.numel() * 4 + arg_host.numel() * 4),
                   "ms_per_step": statistics.mean(e2e_ms)}
 
+    # ---- batched: 64 uneven tiles in one persistent launch, CUDA-graph replay
+    if not args.no_batched:
+        out["batched"] = batched_leg(args, dev)
+
     # ---- CPU oracle on the machine's host cores (bounded sample)
     rate, cores, sample, n, t = oracle_rate(inst, args.cpu_seconds)
     out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -346,6 +375,46 @@ def run_ours(args):
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def batched_leg(args, dev):
+    """The 'batched' workload: 64 tiles with sizes drawn from {512..4096}^2, a sun each
+    (elevation 0.2-3 deg, azimuth 0-360 deg), 50 km rays, one launch; the launch shape
+    is autotuned on every 8th instance and the tuned batch is timed as graph replays
+    (inputs and outputs, ~4 GB, exceed L2)."""
+    import torch
+    import paper_2005_06671_gb300 as ss
+    from paper_2005_06671_gb300 import autotune
+    from workloads import batched_instances
+    t0 = time.perf_counter()
+    insts = batched_instances()
+    gen_s = time.perf_counter() - t0
+    hfs = [ss.Heightfield(torch.from_numpy(d["h"]).to(dev), d["g"], d["radius"]) for d in insts]
+    suns = [ss.Sun(d["suns"][0][0], d["suns"][0][1], d["alpha"]) for d in insts]
+    lmax = insts[0]["lmax"]
+    n_rays = sum(d["h"].size for d in insts)
+    t0 = time.perf_counter()
+    params = autotune.tune_and_store(hfs[::8], suns[::8], lmax, reps=2, rounds=1)
+    tune_s = time.perf_counter() - t0
+    b = ss.Batch(hfs, suns, lmax, **params)
+    b.launch()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    b.close()
+    sizes = sorted({d["h"].shape[0] for d in insts})
+    return {"value": n_rays / (statistics.median(ms) / 1e3), "unit": UNIT,
+            "ms_per_launch": statistics.median(ms), "instances": len(insts), "rays": n_rays,
+            "tile_sizes": sizes, "params": params, "autotune_s": tune_s,
+            "generation_s": gen_s, "graph": True,
+            "includes": "queue reset + 64 maxmip builds + one persistent descent launch"}
 
 
 # ------------------------------------------------------- reference arm

@@ -74,6 +74,15 @@ enum { SS_RAYS_GRID = 0, SS_RAYS_LIST = 1 };
 /* ss_params.flags */
 #define SS_FLAG_COUNT_SAMPLES 0x1u /* fill ss_outputs.counters                      */
 #define SS_FLAG_NO_EARLY_EXIT 0x2u /* ss_shadow_uniform: evaluate every usable sample */
+/* Light-only mode (forward, uniform, batch).  The light depends on c* only
+ * through clamp(c* cos(eps)/alpha, -1, 1) (Eq. discfrac), so the search may use
+ * c_sat = 1.002 alpha / cos(eps): it starts from best = +c_sat (blocks whose
+ * bound reaches it cannot change the light) and stops as soon as
+ * best <= -c_sat (the ray is in full umbra).  light is exact as in the default
+ * mode; argmin and cost are exact for rays in the penumbra; a fully lit ray
+ * reports argmin -1, cost +inf; a ray in umbra reports the first sample found
+ * with cost <= -c_sat (a witness, not necessarily the minimum). */
+#define SS_FLAG_LIGHT_ONLY 0x4u
 
 /* Largest supported tile edge and ray length (samples): sample indices and
  * texel coordinates are exact in float32 below these bounds. */
@@ -183,14 +192,17 @@ ss_status ss_shadow_uniform(const ss_heightfield* hf, const float* mip, const ss
 /* ---------------------------------------------------------- backward
  * Adjoint of light with respect to the heights and the sun direction, at each
  * ray's forward argmin (a subgradient of the minimum; derived from Eq. discfrac
- * and the sample cost).  Inputs: argmin from ss_shadow_forward, grad_light (device
- * [n] float32, dLoss/dlight).  grad_h (device, [ny][pitch] float32) is
- * ACCUMULATED into (zero it first); grad_sun (device double[5]) is accumulated:
- * (dL/d elevation, dL/d azimuth, dL/ds_x, dL/ds_y, dL/ds_z), s a free 3-vector.
- * Rays with j* = -1 or saturated light contribute nothing.  Atomic
- * accumulation: summation order, and so the last bits, may vary between runs. */
+ * and the sample cost).  Inputs: argmin from ss_shadow_forward; cost (optional,
+ * device [n] float32, the forward's cost output) lets rays whose light is
+ * certainly saturated (zero gradient) be skipped before any FP64 work;
+ * grad_light (device [n] float32, dLoss/dlight).  grad_h (device, [ny][pitch]
+ * float32) is ACCUMULATED into (zero it first); grad_sun (device double[5]) is
+ * accumulated: (dL/d elevation, dL/d azimuth, dL/ds_x, dL/ds_y, dL/ds_z), s a
+ * free 3-vector.  Rays with j* = -1 or saturated light contribute nothing.
+ * Atomic accumulation: summation order, and so the last bits, may vary
+ * between runs. */
 ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, const ss_sun* sun,
-                             const ss_params* params, const int32_t* argmin,
+                             const ss_params* params, const int32_t* argmin, const float* cost,
                              const float* grad_light, float* grad_h, double* grad_sun,
                              ss_stream_t stream);
 

@@ -22,6 +22,7 @@ SS_PROJ_GNOMONIC, SS_PROJ_POLAR_STEREO = 0, 1
 SS_RAYS_GRID, SS_RAYS_LIST = 0, 1
 SS_FLAG_COUNT_SAMPLES = 0x1
 SS_FLAG_NO_EARLY_EXIT = 0x2
+SS_FLAG_LIGHT_ONLY = 0x4
 
 
 class SSHeightfield(ctypes.Structure):
@@ -68,7 +69,7 @@ _SIGNATURES = {
     "ss_shadow_uniform": (c_i32, [P(SSHeightfield), c_vp, P(SSRays), P(SSSun), P(SSParams),
                                   P(SSOutputs), c_vp]),
     "ss_shadow_backward": (c_i32, [P(SSHeightfield), P(SSRays), P(SSSun), P(SSParams), c_vp,
-                                   c_vp, c_vp, c_vp, c_vp]),
+                                   c_vp, c_vp, c_vp, c_vp, c_vp]),
     "ss_batch_workspace_bytes": (ctypes.c_size_t, [c_i32]),
     "ss_batch_submit": (c_i32, [c_vp, c_i32, P(SSParams), c_vp, ctypes.c_size_t, c_vp]),
     "ss_batch_plan_create": (c_i32, [c_vp, c_i32, P(SSParams), c_vp, ctypes.c_size_t,

@@ -50,7 +50,8 @@ ss_status check_params(const ss_params* p, double g, int32_t* J, double* delta) 
     if (!p) return SS_ERR_INVALID_ARG;
     if (!finite_pos(p->max_len_m)) return SS_ERR_INVALID_ARG;
     if (!isfinite(p->step_texels) || p->step_texels < 0.0) return SS_ERR_INVALID_ARG;
-    if (p->flags & ~(SS_FLAG_COUNT_SAMPLES | SS_FLAG_NO_EARLY_EXIT)) return SS_ERR_INVALID_ARG;
+    if (p->flags & ~(SS_FLAG_COUNT_SAMPLES | SS_FLAG_NO_EARLY_EXIT | SS_FLAG_LIGHT_ONLY))
+        return SS_ERR_INVALID_ARG;
     if (p->block_threads != 0 &&
         (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32 != 0))
         return SS_ERR_INVALID_ARG;
@@ -109,6 +110,7 @@ ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, doubl
     T.sz = s[2];
     T.delta = delta;
     T.inv_gR = 1.0 / (hf->texel_m * hf->radius_m);
+    T.inv_R = 1.0 / hf->radius_m;
     T.alpha = sun->angular_radius_rad;
     T.delta_f = (float)delta;
     T.inv_delta_f = (float)(1.0 / delta);
@@ -180,7 +182,7 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.flags = params->flags;
     int block = params->block_threads ? params->block_threads : 256;
     a.rays_per_block = (int64_t)block * (params->rays_per_thread > 0 ? params->rays_per_thread : 16);
-    a.refill_min = params->refill_min > 0 ? params->refill_min : 8;
+    a.refill_min = params->refill_min > 0 ? params->refill_min : 6;
     a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
     a.tile_w = params->ray_tile_w;
     if (a.tile_w > 0 && a.rays_per_block % a.tile_w != 0) return SS_ERR_INVALID_ARG;
@@ -261,7 +263,8 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
     B.args.n_items = n;
     B.args.chunk_rays = chunk;
     B.args.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
-    B.args.refill_min = params->refill_min > 0 ? params->refill_min : 8;
+    B.args.refill_min = params->refill_min > 0 ? params->refill_min : 6;
+    B.args.light_only = (params->flags & SS_FLAG_LIGHT_ONLY) ? 1 : 0;
     return SS_OK;
 }
 
@@ -357,7 +360,7 @@ ss_status ss_shadow_uniform(const ss_heightfield* hf, const float* mip, const ss
 }
 
 ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, const ss_sun* sun,
-                             const ss_params* params, const int32_t* argmin,
+                             const ss_params* params, const int32_t* argmin, const float* cost,
                              const float* grad_light, float* grad_h, double* grad_sun,
                              ss_stream_t stream) {
     ss_status st = check_tile(hf, 2);
@@ -378,6 +381,7 @@ ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, cons
     a.R.uv = rays->uv;
     a.R.lift = rays->mode == SS_RAYS_LIST ? rays->lift_m : nullptr;
     a.argmin = argmin;
+    a.cost = cost;
     a.grad_light = grad_light;
     a.grad_h = grad_h;
     a.grad_pitch = hf->pitch;

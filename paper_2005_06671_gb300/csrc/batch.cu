@@ -56,7 +56,7 @@ struct WarpSched {
     float span;         // height span of `cur`
 };
 
-template <bool kCount>
+template <bool kCount, bool kLight>
 __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(const BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
     bool done = false;
     RayF rf;
     Walk w;
-    walk_begin(w);
+    w.best = INFINITY;
+    w.bestj = -1;
     while (true) {
         unsigned act = __ballot_sync(kFull, r >= 0 && !done);
         if (act == 0 || (S.open && S.stash < 0 && __popc(~act) >= a.refill_min)) {
@@ -98,8 +99,8 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                     if (r < 0 && my < cnt) {
                         r = my;
                         const int64_t ray = chunk_ray(S.C, D.T.nx, r);
-                        setup_ray<true>(D.T, grid_rays, ray, S.span, rf);
-                        walk_begin(w);
+                        setup_ray<true, kLight>(D.T, grid_rays, ray, S.span, rf);
+                        walk_begin<kLight>(w, rf, a.kleaf);
                         if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
                             finish_ray(D.T, grid_rays, D.O, ray, w.best, w.bestj, 0, 0);
                             r = -1;
@@ -155,8 +156,8 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
             }
         }
         if (r < 0 || done) continue;
-        done = D.poly ? walk_step<kCount, true, true>(D.T, D.L, D.levels, a.kleaf, rf, w)
-                      : walk_step<kCount, true, false>(D.T, D.L, D.levels, a.kleaf, rf, w);
+        done = D.poly ? walk_step<kCount, true, true, kLight>(D.T, D.L, D.levels, a.kleaf, rf, w)
+                      : walk_step<kCount, true, false, kLight>(D.T, D.L, D.levels, a.kleaf, rf, w);
     }
 }
 
@@ -191,11 +192,15 @@ void batch_layout(void* ws, int32_t n_items, unsigned long long** counter, Batch
 cudaError_t launch_batch_forward(const BatchArgs& a, int block, bool count, cudaStream_t s) {
     const size_t smem = (size_t)(block / 32) * (sizeof(BatchItemDesc) + sizeof(WarpSched));
     if (count) {
-        const int grid = resident_blocks(batch_dp_kernel<true>, block, smem);
-        batch_dp_kernel<true><<<grid, block, smem, s>>>(a);
+        if (a.light_only)
+            batch_dp_kernel<true, true><<<resident_blocks(batch_dp_kernel<true, true>, block, smem), block, smem, s>>>(a);
+        else
+            batch_dp_kernel<true, false><<<resident_blocks(batch_dp_kernel<true, false>, block, smem), block, smem, s>>>(a);
     } else {
-        const int grid = resident_blocks(batch_dp_kernel<false>, block, smem);
-        batch_dp_kernel<false><<<grid, block, smem, s>>>(a);
+        if (a.light_only)
+            batch_dp_kernel<false, true><<<resident_blocks(batch_dp_kernel<false, true>, block, smem), block, smem, s>>>(a);
+        else
+            batch_dp_kernel<false, false><<<resident_blocks(batch_dp_kernel<false, false>, block, smem), block, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

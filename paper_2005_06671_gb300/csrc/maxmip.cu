@@ -2,9 +2,9 @@
 // maximum of the texels it covers one level down).
 //
 // One pass reads a 64x64 tile of its input level with coalesced float4 loads
-// into shared memory and writes the up-to-6 coarser levels of that tile
-// (32x32 ... 1x1) from shared memory, so level 0 is read from HBM exactly once
-// and every coarser level is written once.  Passes repeat on the last level
+// and writes the up-to-6 coarser levels of that tile (32x32 ... 1x1): level 1
+// straight from registers, the rest from shared memory, so level 0 is read
+// from HBM exactly once and every coarser level is written once.  Passes repeat on the last level
 // written until the pyramid reaches 1x1 (4096^2: 2 passes; 16384^2: 3).
 // Children outside the level are ignored (treated as -inf).  Max is exact, so
 // the result is bit-identical to any other evaluation order.
@@ -43,79 +43,88 @@ __device__ __forceinline__ void atomic_min_float(float* addr, float v) {
         atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
 }
 
+// One 64x64 input tile per block.  Thread t owns input rows 2(t/8), 2(t/8)+1
+// and columns 8(t%8) .. 8(t%8)+7: it loads them as four float4 (a warp reads
+// eight full 256-byte row segments), reduces them in registers to four
+// level-1 texels (one float4 store), and leaves the 32x32 level-1 tile in
+// shared memory for the coarser levels.
 template <bool kVec4>
 __global__ void __launch_bounds__(256) mip_pass_kernel(const MipPass a) {
-    __shared__ __align__(16) float buf0[kTile * kTile];
-    __shared__ __align__(16) float buf1[(kTile / 2) * (kTile / 2)];
+    __shared__ __align__(16) float lv1[32 * 32];
+    __shared__ __align__(16) float lv2[16 * 16];
+    __shared__ float wmin[8];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
-    float tmin = INFINITY;
-    if (kVec4) {
-        // 64 rows x 16 float4; in_pitch % 4 == 0 and 16-byte aligned base
+    const int rp = tid >> 3, cb = tid & 7;
+    const int y = y0 + 2 * rp, x = x0 + 8 * cb;
+    float v[2][8];
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-            int idx = it * 256 + tid;
-            int row = idx >> 4, c4 = idx & 15;
-            int y = y0 + row, x = x0 + c4 * 4;
-            float4 v = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
-            if (y < a.in_h) {
-                const float* src = a.in + (int64_t)y * a.in_pitch + x;
-                if (x + 3 < a.in_w) {
-                    v = __ldg(reinterpret_cast<const float4*>(src));
-                } else {
-                    if (x < a.in_w) v.x = __ldg(src);
-                    if (x + 1 < a.in_w) v.y = __ldg(src + 1);
-                    if (x + 2 < a.in_w) v.z = __ldg(src + 2);
-                }
-            }
-            reinterpret_cast<float4*>(buf0)[row * (kTile / 4) + c4] = v;
-            if (a.write_min) {
-                if (y < a.in_h) {
-                    if (x < a.in_w) tmin = fminf(tmin, v.x);
-                    if (x + 1 < a.in_w) tmin = fminf(tmin, v.y);
-                    if (x + 2 < a.in_w) tmin = fminf(tmin, v.z);
-                    if (x + 3 < a.in_w) tmin = fminf(tmin, v.w);
-                }
+    for (int r = 0; r < 2; ++r) {
+        const int yy = y + r;
+        const bool row_ok = yy < a.in_h;
+        const float* src = a.in + (int64_t)yy * a.in_pitch + x;
+        if (kVec4 && row_ok && x + 7 < a.in_w) {
+            const float4 p0 = __ldg(reinterpret_cast<const float4*>(src));
+            const float4 p1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+            v[r][0] = p0.x; v[r][1] = p0.y; v[r][2] = p0.z; v[r][3] = p0.w;
+            v[r][4] = p1.x; v[r][5] = p1.y; v[r][6] = p1.z; v[r][7] = p1.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                v[r][c] = (row_ok && x + c < a.in_w) ? __ldg(src + c) : -INFINITY;
+        }
+    }
+    if (a.write_min) {
+        float m = INFINITY;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (y + r < a.in_h && x + c < a.in_w) m = fminf(m, v[r][c]);
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_down_sync(0xffffffffu, m, o));
+        if ((tid & 31) == 0) wmin[tid >> 5] = m;
+    }
+    // level 1 from registers: texels (x0/2 + 4cb + k, y0/2 + rp), k = 0..3
+    float4 o1;
+    o1.x = fmaxf(fmaxf(v[0][0], v[0][1]), fmaxf(v[1][0], v[1][1]));
+    o1.y = fmaxf(fmaxf(v[0][2], v[0][3]), fmaxf(v[1][2], v[1][3]));
+    o1.z = fmaxf(fmaxf(v[0][4], v[0][5]), fmaxf(v[1][4], v[1][5]));
+    o1.w = fmaxf(fmaxf(v[0][6], v[0][7]), fmaxf(v[1][6], v[1][7]));
+    reinterpret_cast<float4*>(lv1)[rp * 8 + cb] = o1;
+    {
+        const int gx = (x0 >> 1) + 4 * cb, gy = (y0 >> 1) + rp;
+        if (gy < a.out_h[0]) {
+            float* dst = a.out[0] + (int64_t)gy * a.out_pitch[0] + gx;
+            if (gx + 3 < a.out_w[0]) {
+                *reinterpret_cast<float4*>(dst) = o1;   // level pitches are multiples of 4
+            } else {
+                if (gx < a.out_w[0]) dst[0] = o1.x;
+                if (gx + 1 < a.out_w[0]) dst[1] = o1.y;
+                if (gx + 2 < a.out_w[0]) dst[2] = o1.z;
             }
         }
-    } else {
-#pragma unroll 4
-        for (int it = 0; it < 16; ++it) {
-            int idx = it * 256 + tid;
-            int row = idx >> 6, col = idx & 63;
-            int y = y0 + row, x = x0 + col;
-            float v = -INFINITY;
-            if (y < a.in_h && x < a.in_w) {
-                v = __ldg(a.in + (int64_t)y * a.in_pitch + x);
-                tmin = fminf(tmin, v);
-            }
-            buf0[row * kTile + col] = v;
-        }
+        if (a.write_max && a.nlev == 1 && a.out_w[0] == 1 && a.out_h[0] == 1 && gx == 0 && gy == 0)
+            a.stats[0] = o1.x;
     }
     __syncthreads();
-    if (a.write_min) {
-        for (int o = 16; o > 0; o >>= 1) tmin = fminf(tmin, __shfl_down_sync(0xffffffffu, tmin, o));
-        __shared__ float wmin[8];
-        if ((tid & 31) == 0) wmin[tid >> 5] = tmin;
-        __syncthreads();
-        if (tid == 0) {
-            float m = wmin[0];
-            for (int w = 1; w < 8; ++w) m = fminf(m, wmin[w]);
-            if (m < INFINITY) atomic_min_float(a.stats + 1, m);
-        }
+    if (a.write_min && tid == 0) {
+        float m = wmin[0];
+        for (int w = 1; w < 8; ++w) m = fminf(m, wmin[w]);
+        if (m < INFINITY) atomic_min_float(a.stats + 1, m);
     }
-    // successive 2x2 reductions in shared memory: src (size s) -> dst (size s/2)
-    float* src = buf0;
-    float* dst = buf1;
-    int s = kTile;
-    for (int l = 0; l < a.nlev; ++l) {
-        const int h2 = s >> 1;
-        for (int idx = tid; idx < h2 * h2; idx += 256) {
-            int oy = idx / h2, ox = idx - oy * h2;
+    // levels 2.. (16x16 -> 1x1) through shared memory, sizes known at compile time
+    float* src = lv1;
+    float* dst = lv2;
+#pragma unroll
+    for (int l = 1; l < kPassLevels; ++l) {
+        if (l >= a.nlev) break;
+        const int s = kTile >> l, h2 = s >> 1;   // input size s, output size h2
+        if (tid < h2 * h2) {
+            const int oy = tid / h2, ox = tid - oy * h2;
             const float* p = src + (2 * oy) * s + 2 * ox;
-            float m = fmaxf(fmaxf(p[0], p[1]), fmaxf(p[s], p[s + 1]));
-            dst[idx] = m;
-            int gx = (x0 >> (l + 1)) + ox, gy = (y0 >> (l + 1)) + oy;
+            const float m = fmaxf(fmaxf(p[0], p[1]), fmaxf(p[s], p[s + 1]));
+            dst[tid] = m;
+            const int gx = (x0 >> (l + 1)) + ox, gy = (y0 >> (l + 1)) + oy;
             if (gx < a.out_w[l] && gy < a.out_h[l]) {
                 a.out[l][(int64_t)gy * a.out_pitch[l] + gx] = m;
                 if (a.write_max && l == a.nlev - 1 && a.out_w[l] == 1 && a.out_h[l] == 1)
@@ -123,10 +132,9 @@ __global__ void __launch_bounds__(256) mip_pass_kernel(const MipPass a) {
             }
         }
         __syncthreads();
-        float* t = src;   // ping-pong: the level just read becomes the next destination
+        float* t = src;
         src = dst;
         dst = t;
-        s = h2;
     }
 }
 

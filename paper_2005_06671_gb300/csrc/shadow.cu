@@ -49,7 +49,7 @@ __device__ __forceinline__ int32_t draw(const ChunkRange& P, int32_t* s_next, in
 // ---------------------------------------------------------------- descent
 // Each loop iteration is one probe of the exact descent (walk_step) per
 // walking lane.
-template <bool kCount, bool kGrid, bool kPoly>
+template <bool kCount, bool kGrid, bool kPoly, bool kLight>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(const FwdArgs a) {
     __shared__ LevelTab s_lev;
     __shared__ int32_t s_next;
@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
     bool done = false, open = true;
     RayF rf;
     Walk w;
-    walk_begin(w);
+    w.best = INFINITY;
+    w.bestj = -1;
     while (true) {
         unsigned act = __ballot_sync(kFull, r >= 0 && !done);
         if (act == 0 || (open && __popc(~act) >= a.refill_min)) {
@@ -79,8 +80,8 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
                 const int32_t nr = draw(P, &s_next, r, open);
                 if (nr >= 0 && r < 0) {
                     r = nr;
-                    setup_ray<kGrid>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
-                    walk_begin(w);
+                    setup_ray<kGrid, kLight>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
+                    walk_begin<kLight>(w, rf, kleaf);
                     if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
                         finish_ray(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj, 0, 0);
                         r = -1;
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
             }
         }
         if (r < 0 || done) continue;
-        done = walk_step<kCount, kGrid, kPoly>(a.T, s_lev, levels, kleaf, rf, w);
+        done = walk_step<kCount, kGrid, kPoly, kLight>(a.T, s_lev, levels, kleaf, rf, w);
     }
 }
 
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
 // g(t) = (H(t) - max h - G)/t is non-decreasing and bounds every later
 // sample's cost from below; once g(t_j) >= best no later sample can win.
 // G = 3 guards covers the float32 rounding of both sides.
-template <bool kCount, bool kGrid, bool kPoly>
+template <bool kCount, bool kGrid, bool kPoly, bool kLight>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel(const FwdArgs a) {
     __shared__ int32_t s_next;
     const ChunkRange P = block_pool(a, &s_next);
@@ -131,8 +132,8 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel
                 const int32_t nr = draw(P, &s_next, r, open);
                 if (nr >= 0 && r < 0) {
                     r = nr;
-                    setup_ray<kGrid>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
-                    best = INFINITY;
+                    setup_ray<kGrid, kLight>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
+                    best = kLight ? rf.c_sat : INFINITY;
                     bestj = -1;
                     nl = 0;
                     j = rf.j_lo;
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel
             stop = stop || ((h - hmax_rel) - G) / t >= best;
         }
         ++j;
-        done = stop;
+        done = kLight ? (stop || best <= -rf.c_sat) : stop;
     }
 }
 
@@ -184,6 +185,10 @@ __global__ void __launch_bounds__(256) backward_kernel(const BwdArgs a) {
         int32_t j = a.argmin[r];
         float gl = a.grad_light[r];
         if (j < 1 || gl == 0.0f) continue;
+        // the forward's float32 cost rules out rays whose light is certainly
+        // saturated (the same test the forward uses before its FP64 re-evaluation)
+        if (a.cost && fabsf(a.cost[r]) * cos_elev_f32(a.T, a.R, r) >= 1.001f * a.T.alpha_f)
+            continue;
         double up, vp, hp, href, ow[4];
         int32_t oi0, oj0;
         ray_origin(a.T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
@@ -191,10 +196,11 @@ __global__ void __launch_bounds__(256) backward_kernel(const BwdArgs a) {
         geom64(a.T, up, vp, hp, G);
         double U, V;
         double c = leaf_cost64(a.T, G, j, &U, &V);
-        double d = c * G.cos_e / a.T.alpha;
+        const double cos_e = cos_elev(G);
+        double d = c * cos_e / a.T.alpha;
         if (!(d > -1.0 && d < 1.0)) continue;
         double gd = (double)gl * (2.0 / M_PI) * sqrt(1.0 - d * d);   // dL/dd
-        double gc = gd * G.cos_e / a.T.alpha;                         // dL/dc
+        double gc = gd * cos_e / a.T.alpha;                         // dL/dc
         double t = (double)j * a.T.delta;
         // sample texels and the bilinear gradient at (U, V)
         int32_t i0 = (int32_t)floor(U), j0 = (int32_t)floor(V);
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const BwdArgs a) {
         double kq = a.T.R / a.T.g;
         double JU[3] = { kq / q[2], 0.0, -kq * q[0] / (q[2] * q[2]) };
         double JV[3] = { 0.0, kq / q[2], -kq * q[1] / (q[2] * q[2]) };
-        double ce_term = G.cos_e > 0.0 ? (-G.sin_e / G.cos_e) : 0.0;
+        double ce_term = cos_e > 0.0 ? (-G.sin_e / cos_e) : 0.0;
         double gsv[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -295,30 +301,37 @@ static int pool_grid(const FwdArgs& a) {
                             a.R.mode == 0 ? a.tile_w : 0);
 }
 
-template <template <bool, bool, bool> class Launch>
-static cudaError_t dispatch(const FwdArgs& a, int block, cudaStream_t s) {
-    const bool cnt = a.O.counters != nullptr, grid = a.R.mode == 0, poly = a.poly != 0;
-    const int g = pool_grid(a);
-    if (cnt) {
-        if (grid) return poly ? Launch<true, true, true>::go(a, g, block, s) : Launch<true, true, false>::go(a, g, block, s);
-        return poly ? Launch<true, false, true>::go(a, g, block, s) : Launch<true, false, false>::go(a, g, block, s);
-    }
-    if (grid) return poly ? Launch<false, true, true>::go(a, g, block, s) : Launch<false, true, false>::go(a, g, block, s);
-    return poly ? Launch<false, false, true>::go(a, g, block, s) : Launch<false, false, false>::go(a, g, block, s);
-}
+#define SS_FWD_CASE(C, G, P, L) \
+    case ((C) << 3) | ((G) << 2) | ((P) << 1) | (L): return Launch<C, G, P, L>::go(a, grid, block, s);
 
-template <bool C, bool G, bool P>
+// runtime flags -> the kernel instance (counters, grid mode, rise series, light-only)
+template <template <bool, bool, bool, bool> class Launch>
+static cudaError_t dispatch(const FwdArgs& a, int block, cudaStream_t s) {
+    const int idx = ((a.O.counters != nullptr) << 3) | ((a.R.mode == 0) << 2) | ((a.poly != 0) << 1) |
+                    ((a.flags & 0x4u) ? 1 : 0);
+    const int grid = pool_grid(a);
+    switch (idx) {
+        SS_FWD_CASE(0, 0, 0, 0) SS_FWD_CASE(0, 0, 0, 1) SS_FWD_CASE(0, 0, 1, 0) SS_FWD_CASE(0, 0, 1, 1)
+        SS_FWD_CASE(0, 1, 0, 0) SS_FWD_CASE(0, 1, 0, 1) SS_FWD_CASE(0, 1, 1, 0) SS_FWD_CASE(0, 1, 1, 1)
+        SS_FWD_CASE(1, 0, 0, 0) SS_FWD_CASE(1, 0, 0, 1) SS_FWD_CASE(1, 0, 1, 0) SS_FWD_CASE(1, 0, 1, 1)
+        SS_FWD_CASE(1, 1, 0, 0) SS_FWD_CASE(1, 1, 0, 1) SS_FWD_CASE(1, 1, 1, 0) SS_FWD_CASE(1, 1, 1, 1)
+    }
+    return cudaErrorInvalidValue;
+}
+#undef SS_FWD_CASE
+
+template <bool C, bool G, bool P, bool L>
 struct DpLaunch {
     static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
-        dp_forward_kernel<C, G, P><<<grid, block, 0, s>>>(a);
+        dp_forward_kernel<C, G, P, L><<<grid, block, 0, s>>>(a);
         return cudaGetLastError();
     }
 };
 
-template <bool C, bool G, bool P>
+template <bool C, bool G, bool P, bool L>
 struct UniLaunch {
     static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
-        uniform_forward_kernel<C, G, P><<<grid, block, 0, s>>>(a);
+        uniform_forward_kernel<C, G, P, L><<<grid, block, 0, s>>>(a);
         return cudaGetLastError();
     }
 };

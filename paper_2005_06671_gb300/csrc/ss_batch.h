@@ -32,6 +32,7 @@ struct BatchArgs {
     int32_t chunk_rays;
     int32_t kleaf;
     int32_t refill_min;
+    int32_t light_only;             // SS_FLAG_LIGHT_ONLY
 };
 
 constexpr size_t kBatchHeader = 256;   // queue counter, padded

@@ -45,6 +45,7 @@ struct Tile {
     double sx, sy, sz;         // sun direction
     double delta;              // sample spacing (m)
     double inv_gR;             // 1 / (g R)
+    double inv_R;              // 1 / R
     double alpha;              // sun angular radius
     float delta_f;             // (float)delta
     float inv_delta_f;         // (float)(1/delta)
@@ -69,8 +70,8 @@ struct Outputs {
 struct Geom64 {
     double up, vp;             // origin texel coordinates
     double hp, href;           // origin height, reference texel height
-    double rho;                // R + h_p
-    double sin_e, cos_e;       // sun elevation over the radial normal at p
+    double rho, inv_rho;       // R + h_p and its reciprocal
+    double sin_e;              // sun elevation over the radial normal at p
     double nhat[3];            // radial unit normal at p
     double Au, Av, b;          // u_j = u_p + Au * j/(1 + b j), same for v
     int32_t oi0, oj0;          // origin bilinear base texel
@@ -91,6 +92,7 @@ struct RayF {
     float tv;                  // distance of the lowest ray point (sin_e < 0), else -1
     float guard0;              // |X| + height span of the tile
     float pos_eps;             // footprint margin covering float32 block-end positions
+    float c_sat;               // light-only mode: 1.002 alpha / cos(eps_p)
     int32_t j_lo, j_hi;        // usable sample range (empty when j_lo > j_hi)
 };
 
@@ -149,9 +151,10 @@ __device__ __forceinline__ void ray_origin(const Tile& T, const Rays& R, int64_t
 // FP64 local frame of a ray whose origin is at texel coords (up, vp), height hp.
 __device__ __forceinline__ void geom64(const Tile& T, double up, double vp, double hp,
                                        Geom64& G) {
-    double Xp = (up - T.cx) * T.g, Yp = (vp - T.cy) * T.g;
-    double m = sqrt(Xp * Xp + Yp * Yp + T.R * T.R);
-    double im = 1.0 / m;
+    const double Xp = (up - T.cx) * T.g, Yp = (vp - T.cy) * T.g;
+    const double m2 = Xp * Xp + Yp * Yp + T.R * T.R;
+    const double im = rsqrt(m2);              // 1/|(X, Y, R)|
+    const double m = m2 * im;
     G.up = up;
     G.vp = vp;
     G.hp = hp;
@@ -159,46 +162,60 @@ __device__ __forceinline__ void geom64(const Tile& T, double up, double vp, doub
     G.nhat[1] = Yp * im;
     G.nhat[2] = T.R * im;
     G.sin_e = (Xp * T.sx + Yp * T.sy + T.R * T.sz) * im;
-    G.cos_e = sqrt(fmax(0.0, 1.0 - G.sin_e * G.sin_e));
     G.rho = T.R + hp;
-    double f = T.delta * m / G.rho;           // sample index -> t' along the ray
-    double k = f * T.inv_gR;
+    G.inv_rho = 1.0 / G.rho;
+    const double f = T.delta * m * G.inv_rho; // sample index -> t' along the ray
+    const double k = f * T.inv_gR;
     G.Au = k * (T.R * T.sx - T.sz * Xp);
     G.Av = k * (T.R * T.sy - T.sz * Yp);
-    G.b = f * T.sz / T.R;
+    G.b = f * T.sz * T.inv_R;
 }
 
-// tau(j) = j/(1 + b j); the inverse is j = tau/(1 - b tau).
-__device__ __forceinline__ double tau_to_j(double tau, double b) {
-    double den = 1.0 - b * tau;
-    return den > 0.0 ? tau / den : INFINITY;
+__device__ __forceinline__ double cos_elev(const Geom64& G) {
+    return sqrt(fmax(0.0, 1.0 - G.sin_e * G.sin_e));
 }
 
-// Usable sample range: texel image inside [0,nx-1]x[0,ny-1] (clip of the line
-// u_p + Au tau, v_p + Av tau against the box), intersected with [1, J].
+// Sample index at which u_p + a j/(1 + b j) reaches boundary B (j = (B - u_p) /
+// (a - b (B - u_p))); +inf when it never does.
+__device__ __forceinline__ double cross_j(double p0, double a, double b, double B) {
+    const double d = B - p0;
+    const double den = a - b * d;
+    return (den != 0.0 && d / den >= 0.0) ? d / den : INFINITY;
+}
+
+// Usable sample range: texel image inside [0,nx-1]x[0,ny-1], intersected with
+// [1, J].  The image is a straight texel line traversed monotonically, so the
+// usable samples are one run; origins inside the tile (grid mode, usual list
+// mode) only need the exit, one division per axis.
 __device__ __forceinline__ void sample_range(const Tile& T, const Geom64& G, int32_t& j_lo,
                                              int32_t& j_hi) {
-    double tlo = 0.0, thi = INFINITY;
-    bool empty = false;
     const double p0[2] = { G.up, G.vp }, a[2] = { G.Au, G.Av };
     const double hi[2] = { (double)(T.nx - 1), (double)(T.ny - 1) };
+    const bool inside = p0[0] >= 0.0 && p0[0] <= hi[0] && p0[1] >= 0.0 && p0[1] <= hi[1];
+    double jl = 0.0, jh = INFINITY;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        if (a[k] == 0.0) {
-            if (p0[k] < 0.0 || p0[k] > hi[k]) empty = true;
+        if (inside) {
+            if (a[k] != 0.0) jh = fmin(jh, cross_j(p0[k], a[k], G.b, a[k] > 0.0 ? hi[k] : 0.0));
+        } else if (a[k] == 0.0) {
+            if (p0[k] < 0.0 || p0[k] > hi[k]) jh = -1.0;   // never enters
         } else {
-            double ia = 1.0 / a[k];
-            double t1 = (0.0 - p0[k]) * ia, t2 = (hi[k] - p0[k]) * ia;
-            tlo = fmax(tlo, fmin(t1, t2));
-            thi = fmin(thi, fmax(t1, t2));
+            const double j0 = cross_j(p0[k], a[k], G.b, 0.0);
+            const double j1 = cross_j(p0[k], a[k], G.b, hi[k]);
+            const bool below = (a[k] > 0.0) ? (p0[k] < 0.0) : (p0[k] > hi[k]);
+            const bool above = (a[k] > 0.0) ? (p0[k] > hi[k]) : (p0[k] < 0.0);
+            if (above) jh = -1.0;                         // moving away from the tile
+            const double enter = below ? (a[k] > 0.0 ? j0 : j1) : 0.0;
+            const double leave = a[k] > 0.0 ? j1 : j0;
+            jl = fmax(jl, enter);
+            jh = fmin(jh, leave);
         }
     }
-    if (empty || !(thi >= tlo)) {
+    if (!(jh >= jl) || jh < 1.0) {
         j_lo = 1;
         j_hi = 0;
         return;
     }
-    double jl = tau_to_j(tlo, G.b), jh = tau_to_j(thi, G.b);
     j_lo = (int32_t)fmax(1.0, ceil(jl));
     j_hi = (int32_t)fmin((double)T.J, floor(jh));
 }
@@ -214,8 +231,8 @@ __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double
     split8(G.Av, r.av_hi, r.av_lo);
     r.b = (float)G.b;
     r.B = (float)(2.0 * G.rho * G.sin_e);
-    r.inv_2rho = (float)(0.5 / G.rho);
-    r.inv_rho2 = (float)(1.0 / (G.rho * G.rho));
+    r.inv_2rho = (float)(0.5 * G.inv_rho);
+    r.inv_rho2 = (float)(G.inv_rho * G.inv_rho);
     r.X = (float)(G.hp - href);
     r.href = (float)href;
     r.tv = G.sin_e < 0.0 ? (float)(-G.rho * G.sin_e) : -1.0f;

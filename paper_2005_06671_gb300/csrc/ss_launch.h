@@ -39,6 +39,7 @@ struct BwdArgs {
     Tile T;
     Rays R;
     const int32_t* argmin;
+    const float* cost;          // optional forward cost (saturation pre-test)
     const float* grad_light;
     float* grad_h;
     int64_t grad_pitch;

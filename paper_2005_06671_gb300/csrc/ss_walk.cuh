@@ -58,7 +58,7 @@ __device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const O
         Geom64 G;
         geom64(T, up, vp, hp, G);
         double c = leaf_cost64(T, G, bestj);
-        light = (float)disc_light64(c * G.cos_e / T.alpha);
+        light = (float)disc_light64(c * cos_elev(G) / T.alpha);
         cost = (float)c;
     }
     O.light[r] = light;
@@ -70,7 +70,7 @@ __device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const O
     }
 }
 
-template <bool kGrid>
+template <bool kGrid, bool kLight = false>
 __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t r, float span,
                                           RayF& rf) {
     double up, vp, hp, href;
@@ -88,6 +88,11 @@ __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t 
     geom64(T, up, vp, hp, G);
     make_rayf(T, G, href, span, rf);
     if (kGrid) rf.X = 0.0f;
+    if (kLight) {   // saturation threshold of the light (with a 0.2% margin)
+        const float se = (float)G.sin_e;
+        const float ce = sqrtf(fmaxf(0.0f, 1.0f - se * se));
+        rf.c_sat = ce > 0.0f ? 1.002f * T.alpha_f / ce : INFINITY;
+    }
 }
 
 
@@ -148,11 +153,20 @@ struct Walk {
 
 // While best is +inf every block on the left spine of the tree is split without
 // a bound being able to prune it, so the walk starts directly with the first
-// run of leaves (same order, same result).
-__device__ __forceinline__ void walk_begin(Walk& w) {
-    w.best = INFINITY;
+// run of leaves (same order, same result).  In light-only mode best starts at
+// +c_sat, which can prune from the root, so the walk starts at the root.
+template <bool kLight = false>
+__device__ __forceinline__ void walk_begin(Walk& w, const RayF& rf, int32_t kleaf) {
     w.bestj = -1;
-    w.s0 = w.k = w.nb = w.nl = 0;
+    w.s0 = w.nb = w.nl = 0;
+    if (kLight) {
+        w.best = rf.c_sat;
+        const int32_t K = rf.j_hi <= 1 ? 0 : 32 - __clz(rf.j_hi - 1);   // 2^K >= j_hi
+        w.k = K > kleaf ? K : 0;
+    } else {
+        w.best = INFINITY;
+        w.k = 0;
+    }
 }
 
 // One probe of the exact descent and the state update; true when finished.
@@ -163,7 +177,7 @@ __device__ __forceinline__ void walk_begin(Walk& w) {
 // k = ctz(s0), the next block in near-to-far order, so samples are evaluated
 // in increasing j and a strict '<' keeps the smallest j among equal costs.
 // Blocks are clipped to [j_lo, j_hi].
-template <bool kCount, bool kGrid, bool kPoly>
+template <bool kCount, bool kGrid, bool kPoly, bool kLight = false>
 __device__ __forceinline__ bool walk_step(const Tile& T, const LevelTab& L, int32_t levels,
                                           int32_t kleaf, const RayF& rf, Walk& w) {
     const bool leaf = (w.k == 0);
@@ -186,7 +200,8 @@ __device__ __forceinline__ bool walk_step(const Tile& T, const LevelTab& L, int3
     const int32_t k_adv = __ffs(s_adv) - 1;
     w.s0 = descend ? w.s0 : s_adv;
     w.k = descend ? ((w.k - 1 > kleaf) ? w.k - 1 : 0) : ((k_adv <= kleaf) ? 0 : k_adv);
-    return !descend && (s_adv >= rf.j_hi);
+    const bool end = !descend && (s_adv >= rf.j_hi);
+    return kLight ? (end || w.best <= -rf.c_sat) : end;
 }
 
 }  // namespace ss

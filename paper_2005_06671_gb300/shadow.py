@@ -14,7 +14,7 @@ import torch
 
 from . import _abi
 from ._abi import (SSHeightfield, SSOutputs, SSParams, SSRays, SSSun, check,
-                   SS_FLAG_COUNT_SAMPLES, SS_FLAG_NO_EARLY_EXIT)
+                   SS_FLAG_COUNT_SAMPLES, SS_FLAG_NO_EARLY_EXIT, SS_FLAG_LIGHT_ONLY)
 
 PROJ = {"gnomonic": _abi.SS_PROJ_GNOMONIC, "polar_stereo": _abi.SS_PROJ_POLAR_STEREO}
 
@@ -159,9 +159,10 @@ def _forward(fn_name, hf, mip, sun, max_len_m, step_texels, uv, lift, flags, blo
 def ss_shadow_forward(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
                       lift=None, count_samples=False, block_threads=0, leaf_level=-1,
                       want_cost=True, out=None, stream=None, rays_per_thread=0, refill_min=0,
-                      ray_tile_w=0):
-    """Exact max-mip descent.  Returns dict(light, argmin, cost, counters)."""
-    flags = SS_FLAG_COUNT_SAMPLES if count_samples else 0
+                      ray_tile_w=0, light_only=False):
+    """Exact max-mip descent.  Returns dict(light, argmin, cost, counters).
+    light_only: saturation cutoffs (exact light; argmin/cost exact in the penumbra)."""
+    flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (SS_FLAG_LIGHT_ONLY if light_only else 0)
     return _forward("ss_shadow_forward", hf, mip, sun, max_len_m, step_texels, uv, lift, flags,
                     block_threads, leaf_level, want_cost, out, stream, rays_per_thread,
                     refill_min, ray_tile_w)
@@ -170,9 +171,10 @@ def ss_shadow_forward(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5
 def ss_shadow_uniform(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
                       lift=None, count_samples=False, early_exit=True, block_threads=0,
                       want_cost=True, out=None, stream=None, rays_per_thread=0, refill_min=0,
-                      ray_tile_w=0):
+                      ray_tile_w=0, light_only=False):
     """Uniform stepping over every sample (exact early exit unless disabled)."""
-    flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (0 if early_exit else SS_FLAG_NO_EARLY_EXIT)
+    flags = ((SS_FLAG_COUNT_SAMPLES if count_samples else 0) |
+             (0 if early_exit else SS_FLAG_NO_EARLY_EXIT) | (SS_FLAG_LIGHT_ONLY if light_only else 0))
     return _forward("ss_shadow_uniform", hf, mip, sun, max_len_m, step_texels, uv, lift, flags,
                     block_threads, -1, want_cost, out, stream, rays_per_thread, refill_min,
                     ray_tile_w)
@@ -181,9 +183,10 @@ def ss_shadow_uniform(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5
 # ---------------------------------------------------------------- backward
 def ss_shadow_backward(hf: Heightfield, sun: Sun, max_len_m, argmin, grad_light, step_texels=0.5,
                        uv=None, lift=None, grad_h=None, grad_sun=None, block_threads=0,
-                       stream=None):
+                       stream=None, cost=None):
     """Accumulates dL/dh into grad_h [ny, nx] (float32) and dL/d(elev, az, s_x, s_y, s_z)
-    into grad_sun (float64 [5]); allocates zeroed ones when not given."""
+    into grad_sun (float64 [5]); allocates zeroed ones when not given.  ``cost``
+    (the forward's cost output) lets saturated rays be skipped early."""
     rays, n = _rays(hf, uv, lift)
     if grad_h is None:
         grad_h = torch.zeros_like(hf.h)
@@ -194,9 +197,10 @@ def ss_shadow_backward(hf: Heightfield, sun: Sun, max_len_m, argmin, grad_light,
     argmin = argmin.contiguous()
     grad_light = grad_light.to(torch.float32).contiguous()
     prm = _params(max_len_m, step_texels, 0, block_threads, -1)
+    cost = None if cost is None else cost.contiguous()
     check(_abi.lib().ss_shadow_backward(ctypes.byref(hf.c()), ctypes.byref(rays),
                                         ctypes.byref(sun.c()), ctypes.byref(prm),
-                                        _ptr(argmin), _ptr(grad_light), _ptr(grad_h),
+                                        _ptr(argmin), _ptr(cost), _ptr(grad_light), _ptr(grad_h),
                                         _ptr(grad_sun), _stream_ptr(stream)),
           "ss_shadow_backward")
     return grad_h, grad_sun
@@ -218,8 +222,8 @@ class ShadowFn(torch.autograd.Function):
         hf = Heightfield(h.detach().contiguous(), texel_m, radius_m)
         sun = Sun(e, a, alpha)
         mip = ss_build_maxmip(hf)
-        res = ss_shadow_forward(hf, mip, sun, max_len_m, step_texels, want_cost=False)
-        ctx.save_for_backward(hf.h, res["argmin"])
+        res = ss_shadow_forward(hf, mip, sun, max_len_m, step_texels, want_cost=True)
+        ctx.save_for_backward(hf.h, res["argmin"], res["cost"])
         ctx.geom = (texel_m, radius_m, alpha, max_len_m, step_texels, e, a)
         ctx.sun_dtype = sun_angles.dtype
         ctx.sun_device = sun_angles.device
@@ -227,11 +231,11 @@ class ShadowFn(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_light):
-        h, argmin = ctx.saved_tensors
+        h, argmin, cost = ctx.saved_tensors
         texel_m, radius_m, alpha, max_len_m, step_texels, e, a = ctx.geom
         hf = Heightfield(h, texel_m, radius_m)
         gh, gs = ss_shadow_backward(hf, Sun(e, a, alpha), max_len_m, argmin,
-                                    grad_light.contiguous(), step_texels)
+                                    grad_light.contiguous(), step_texels, cost=cost)
         g_sun = gs[:2].to(device=ctx.sun_device, dtype=ctx.sun_dtype)
         return gh, g_sun, None, None, None, None, None
 
@@ -251,12 +255,12 @@ class Batch:
 
     def __init__(self, hfs, suns, max_len_m, step_texels=0.5, count_samples=False,
                  want_cost=False, block_threads=0, leaf_level=-1, rays_per_thread=0,
-                 refill_min=0, ray_tile_w=0):
+                 refill_min=0, ray_tile_w=0, light_only=False):
         if len(hfs) != len(suns) or not hfs:
             raise ValueError("need one sun per heightfield, at least one item")
         self.hfs, self.suns = list(hfs), list(suns)
         dev = hfs[0].h.device
-        flags = SS_FLAG_COUNT_SAMPLES if count_samples else 0
+        flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (SS_FLAG_LIGHT_ONLY if light_only else 0)
         self.params = SSParams(float(max_len_m), float(step_texels), int(flags), int(block_threads),
                                int(leaf_level), int(rays_per_thread), int(refill_min),
                                int(ray_tile_w), 0)

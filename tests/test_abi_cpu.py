@@ -134,9 +134,10 @@ def test_other_entry_points_reject_bad_arguments():
     assert lib.ss_shadow_uniform(ctypes.byref(hf), None, ctypes.byref(rays), ctypes.byref(sun),
                                  ctypes.byref(prm), ctypes.byref(out), None) == 1
     assert lib.ss_shadow_backward(ctypes.byref(hf), ctypes.byref(rays), ctypes.byref(sun),
-                                  ctypes.byref(prm), None, ctypes.c_void_p(FAKE),
+                                  ctypes.byref(prm), None, None, ctypes.c_void_p(FAKE),
                                   ctypes.c_void_p(FAKE), ctypes.c_void_p(FAKE), None) == 1
     prm.max_len_m = -1.0
     assert lib.ss_shadow_backward(ctypes.byref(hf), ctypes.byref(rays), ctypes.byref(sun),
-                                  ctypes.byref(prm), ctypes.c_void_p(FAKE), ctypes.c_void_p(FAKE),
-                                  ctypes.c_void_p(FAKE), ctypes.c_void_p(FAKE), None) == 1
+                                  ctypes.byref(prm), ctypes.c_void_p(FAKE), None,
+                                  ctypes.c_void_p(FAKE), ctypes.c_void_p(FAKE),
+                                  ctypes.c_void_p(FAKE), None) == 1

@@ -26,7 +26,7 @@ def _dev(a):
 
 
 def _run(h, g, sun, lmax, step=0.5, method="dp", uv=None, lift=None, count=False,
-         early_exit=True, hpad=0, leaf_level=-1, block_threads=0):
+         early_exit=True, hpad=0, leaf_level=-1, block_threads=0, light_only=False):
     ny, nx = h.shape
     if hpad:
         store = torch.full((ny, nx + hpad), float("nan"), device="cuda")
@@ -41,10 +41,12 @@ def _run(h, g, sun, lmax, step=0.5, method="dp", uv=None, lift=None, count=False
     lt = None if lift is None else _dev(lift)
     if method == "dp":
         res = ss.ss_shadow_forward(hf, mip, s, lmax, step, uv=uvt, lift=lt, count_samples=count,
-                                   leaf_level=leaf_level, block_threads=block_threads)
+                                   leaf_level=leaf_level, block_threads=block_threads,
+                                   light_only=light_only)
     else:
         res = ss.ss_shadow_uniform(hf, mip, s, lmax, step, uv=uvt, lift=lt, count_samples=count,
-                                   early_exit=early_exit, block_threads=block_threads)
+                                   early_exit=early_exit, block_threads=block_threads,
+                                   light_only=light_only)
     torch.cuda.synchronize()
     return {k: (None if v is None else v.cpu().numpy()) for k, v in res.items()}
 
@@ -191,6 +193,20 @@ def test_edge_cases():
     ids = random_ids(h.size, 300, seed=5)
     compare_to_oracle(h, 15.0, R, sun, 65535 * 7.5, 0.5, out["light"][ids], out["argmin"][ids],
                       out["cost"][ids], ray_ids=ids)
+    # listed origins outside the tile: rays that enter it, rays that never do
+    rng = np.random.default_rng(17)
+    uv_out = np.concatenate([
+        np.stack([rng.uniform(-40, -1, 200), rng.uniform(0, 60, 200)], 1),
+        np.stack([rng.uniform(97, 140, 200), rng.uniform(0, 60, 200)], 1),
+        np.stack([rng.uniform(0, 96, 200), rng.uniform(-30, -0.5, 200)], 1),
+    ]).astype(np.float32)
+    lift_out = rng.uniform(0, 200, uv_out.shape[0]).astype(np.float32)
+    for az in (211.0, 60.0, 300.0):
+        sun_o = (math.radians(1.3), math.radians(az), ALPHA)
+        for method in ("dp", "uniform"):
+            out = _run(h, 15.0, sun_o, 3000.0, method=method, uv=uv_out, lift=lift_out)
+            compare_to_oracle(h, 15.0, R, sun_o, 3000.0, 0.5, out["light"], out["argmin"],
+                              out["cost"], uv=uv_out, lift=lift_out)
     # empty ray list
     hf = ss.Heightfield(_dev(h), 15.0, R)
     mip = ss.ss_build_maxmip(hf)
@@ -226,8 +242,8 @@ def _grad_case(n=96, k_sun=1):
     return h, g, (elev, az, alpha), 3000.0
 
 
-@pytest.mark.parametrize("k_sun", [0, 1, 2, 3])
-def test_backward_vs_oracle_gradient(k_sun):
+@pytest.mark.parametrize("k_sun,pass_cost", [(0, False), (1, True), (2, False), (3, True)])
+def test_backward_vs_oracle_gradient(k_sun, pass_cost):
     h, g, sun, lmax = _grad_case(k_sun=k_sun)
     ht = _dev(h)
     hf = ss.Heightfield(ht, g, R)
@@ -239,7 +255,8 @@ def test_backward_vs_oracle_gradient(k_sun):
     gl = np.random.default_rng(3 + k_sun).normal(size=h.size)
     gl[am_gpu != oa] = 0.0          # tie rays: the two argmins give different subgradients
     gh_gpu, gs_gpu = ss.ss_shadow_backward(hf, s, lmax, res["argmin"],
-                                           torch.from_numpy(gl.astype(np.float32)).cuda())
+                                           torch.from_numpy(gl.astype(np.float32)).cuda(),
+                                           cost=res["cost"] if pass_cost else None)
     torch.cuda.synchronize()
     gh_o, gs_o = oracle.grad(h, g, R, sun[0], sun[1], sun[2], oa,
                              gl.astype(np.float32).astype(np.float64))
@@ -265,3 +282,35 @@ def test_autograd_function_matches_oracle():
     scale = np.abs(gh_o).max()
     assert np.abs(gh.cpu().numpy() - gh_o).max() <= 1e-4 * scale
     np.testing.assert_allclose(gang.numpy(), gs_o[:2], rtol=1e-4, atol=1e-7)
+
+
+# ------------------------------------------------ light-only (saturation cutoffs)
+@pytest.mark.parametrize("name,n", [("tiny", None), ("mid", 1024), ("diff", 512)])
+def test_light_only_mode_vs_oracle(name, n):
+    """Light-only mode: light exact (1e-5 of the oracle); in the penumbra the
+    argmin and cost are the exact ones; fully lit rays report argmin -1; rays in
+    umbra report a witness sample whose oracle cost proves the umbra."""
+    import oracle as orc
+    inst = make_instance(name, n=n)
+    h, g = inst["h"], inst["g"]
+    for (elev, az) in inst["suns"][:2]:
+        sun = (elev, az, inst["alpha"])
+        exact = _run(h, g, sun, inst["lmax"])
+        for method in ("dp", "uniform"):
+            lo = _run(h, g, sun, inst["lmax"], method=method, light_only=True)
+            assert np.abs(lo["light"] - exact["light"]).max() <= LIGHT_TOL
+            pen = (exact["light"] > 0) & (exact["light"] < 1)
+            assert np.array_equal(lo["argmin"][pen], exact["argmin"][pen])
+            lit = exact["light"] == 1
+            assert np.all((lo["argmin"][lit] == -1) | (lo["argmin"][lit] == exact["argmin"][lit]))
+        ids = random_ids(h.size, 1500, seed=55)
+        compare_to_oracle(h, g, R, sun, inst["lmax"], 0.5, lo["light"][ids], exact["argmin"][ids],
+                          exact["cost"][ids], ray_ids=ids)
+        # umbra witnesses: the oracle's cost at the reported sample is below -alpha/cos(eps)
+        dark = np.nonzero(exact["light"] == 0)[0][:40]
+        sinp = orc.sin_elev(h, g, R, sun[0], sun[1])
+        for r in dark:
+            cs = orc.ray_costs(h, g, R, sun[0], sun[1], inst["lmax"], r % h.shape[1],
+                               r // h.shape[1])
+            j = lo["argmin"][r]
+            assert j >= 1 and cs[j - 1] * math.sqrt(1 - sinp[r] ** 2) <= -inst["alpha"]
