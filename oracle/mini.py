@@ -94,6 +94,11 @@ def shadow(h, g, radius, elev, az, alpha, lmax, step_texels=0.5, proj="gnomonic"
         ok &= (us >= 0) & (us <= nx - 1) & (vs >= 0) & (vs <= ny - 1)
         if not ok.any():
             continue
+        # only the first run of in-tile samples: the ray is not followed after it leaves
+        first = int(np.argmax(ok))
+        after = np.nonzero(~ok[first:])[0]
+        if after.size:
+            ok[first + after[0]:] = False
         H = np.linalg.norm(q, axis=1) - radius
         c = np.full(J, np.inf)
         c[ok] = (H[ok] - _bilerp(h, us[ok], vs[ok])) / t[ok]

@@ -34,7 +34,12 @@
  *   sun: s = (cos e sin a, cos e cos a, sin e), elevation e and azimuth a (from
  *   grid +y toward +x) in the tile-centre frame.
  *   samples t_j = j * delta, j = 1..floor(Lmax / delta), delta = step_texels * g.
- *   A sample is used when its texel coordinates lie in [0,nx-1] x [0,ny-1].
+ *   A sample is used when its texel coordinates lie in [0,nx-1] x [0,ny-1] and
+ *   the ray has not left the tile before it: only the first run of in-tile
+ *   samples counts (reading: a shadow ray is followed until its image leaves
+ *   the heightfield; for gnomonic tiles, where the image is a straight line,
+ *   that run is every in-tile sample; on polar stereographic tiles the image
+ *   is a circle arc that could re-enter, and re-entries are not followed).
  *   Bilinear: base = min(floor(u), nx-2), frac = u - base.
  *   Ties: the smallest j among equal costs.  No usable sample: cost = +inf,
  *   argmin = -1, light = 1.
@@ -203,11 +208,17 @@ static void ray_forward(const or_tile* t, const or_sun* sun, const double s[3],
     int64_t J = n_samples(lmax, delta);
     double best = INFINITY;
     int64_t bj = -1;
+    int seen = 0;
     for (int64_t j = 1; j <= J; ++j) {
         double c;
-        if (sample_cost(t, &o, s, (double)j * delta, &c) && c < best) {
-            best = c;
-            bj = j;
+        if (sample_cost(t, &o, s, (double)j * delta, &c)) {
+            seen = 1;
+            if (c < best) {
+                best = c;
+                bj = j;
+            }
+        } else if (seen) {
+            break;   /* the ray has left the tile: it is not followed further */
         }
     }
     double se = dot3(o.n, s);
@@ -268,9 +279,13 @@ int64_t or_ray_costs(const double* h, int32_t nx, int32_t ny, int64_t pitch, dou
     make_origin(&t, u, v, lift, &o);
     double delta = step_texels * g;
     int64_t J = n_samples(lmax, delta);
+    int seen = 0, left = 0;
     for (int64_t j = 1; j <= J && j <= max_out; ++j) {
         double c;
-        costs[j - 1] = sample_cost(&t, &o, s, (double)j * delta, &c) ? c : NAN;
+        int ok = !left && sample_cost(&t, &o, s, (double)j * delta, &c);
+        if (ok) seen = 1;
+        else if (seen) left = 1;
+        costs[j - 1] = ok ? c : NAN;
     }
     return J;
 }
