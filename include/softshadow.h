@@ -21,7 +21,11 @@
  * Y = (v - (ny-1)/2)*g, mapped to the sphere gnomonically (direction
  * (X, Y, R)/|.|; a straight 3-D ray maps to a straight texture line, Sec. 3.2,
  * Appendix "Deriving T") or by polar stereographic projection (tile centred on
- * the pole).  Heights h are metres above the sphere.  Bilinear interpolation
+ * the pole, projected from the antipode onto the plane z = R: direction
+ * (4RX, 4RY, 4R^2 - X^2 - Y^2)/(4R^2 + X^2 + Y^2); a ray maps to a circular
+ * arc).  ss_shadow_forward, ss_shadow_uniform and ss_shadow_backward take either
+ * mapping; the batch calls take gnomonic tiles only (SS_ERR_UNSUPPORTED
+ * otherwise).  Heights h are metres above the sphere.  Bilinear interpolation
  * uses base texel min(floor(u), nx-2); the usable domain is [0,nx-1]x[0,ny-1].
  * Sun direction s = (cos e sin a, cos e cos a, sin e) in the tile frame:
  * elevation e, azimuth a measured from grid +y toward grid +x.

@@ -114,6 +114,7 @@ ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, doubl
     T.alpha = sun->angular_radius_rad;
     T.delta_f = (float)delta;
     T.inv_delta_f = (float)(1.0 / delta);
+    T.sz_f = (float)s[2];
     T.alpha_f = (float)sun->angular_radius_rad;
     return T;
 }
@@ -153,7 +154,6 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
                         const ss_outputs* out, ss_stream_t stream) {
     ss_status st = check_tile(hf, 2);
     if (st != SS_OK) return st;
-    if (hf->projection != SS_PROJ_GNOMONIC) return SS_ERR_UNSUPPORTED;
     if ((st = check_sun(sun)) != SS_OK) return st;
     int32_t J;
     double delta;
@@ -365,7 +365,6 @@ ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, cons
                              ss_stream_t stream) {
     ss_status st = check_tile(hf, 2);
     if (st != SS_OK) return st;
-    if (hf->projection != SS_PROJ_GNOMONIC) return SS_ERR_UNSUPPORTED;
     if ((st = check_sun(sun)) != SS_OK) return st;
     int32_t J;
     double delta;

@@ -49,6 +49,7 @@ struct Tile {
     double alpha;              // sun angular radius
     float delta_f;             // (float)delta
     float inv_delta_f;         // (float)(1/delta)
+    float sz_f;                // (float)sz
     float alpha_f;
 };
 
@@ -73,7 +74,10 @@ struct Geom64 {
     double rho, inv_rho;       // R + h_p and its reciprocal
     double sin_e;              // sun elevation over the radial normal at p
     double nhat[3];            // radial unit normal at p
-    double Au, Av, b;          // u_j = u_p + Au * j/(1 + b j), same for v
+    double Au, Av, b;          // gnomonic: u_j = u_p + Au * j/(1 + b j), same for v
+    double Bu, Bv, inv_a0;     // stereographic: u_j = u_p + (Au j - Bu w)/(1 + w inv_a0),
+                               //   w = rise(t_j) + t_j s_z, a0 = |p| + p_z
+    double nz_cross;           // stereographic: |z of unit(p x s)| (image circle curvature)
     int32_t oi0, oj0;          // origin bilinear base texel
     double ow[4];              // origin bilinear weights (i0,j0),(i0+1,j0),(i0,j0+1),(i0+1,j0+1)
 };
@@ -93,6 +97,8 @@ struct RayF {
     float guard0;              // |X| + height span of the tile
     float pos_eps;             // footprint margin covering float32 block-end positions
     float c_sat;               // light-only mode: 1.002 alpha / cos(eps_p)
+    float bu, bv;              // stereographic: texels per metre of w (see Geom64)
+    float inv8r;               // stereographic: 1/(8 r) of the image circle (texels^-1)
     int32_t j_lo, j_hi;        // usable sample range (empty when j_lo > j_hi)
 };
 
@@ -171,6 +177,73 @@ __device__ __forceinline__ void geom64(const Tile& T, double up, double vp, doub
     G.b = f * T.sz * T.inv_R;
 }
 
+// Polar stereographic tile (centred on the pole, plane z = R, projection from
+// the antipode): direction n = (4RX, 4RY, 4R^2 - r^2)/(4R^2 + r^2).  A point q
+// maps to X = 2R q_x/(|q| + q_z); with q = p + t s, |q| = |p| + rise(t):
+//   X(t) - X_p = (t (2R s_x/a0) - w (2R p_x/a0^2)) / (1 + w/a0),
+//   a0 = |p| + p_z, w = rise(t) + t s_z,
+// which is free of cancellation.  The image of the ray is an arc of a circle
+// of radius 2R / |z of unit(p x s)| (great circles map to circles).
+__device__ __forceinline__ void geom64_stereo(const Tile& T, double up, double vp, double hp,
+                                              Geom64& G) {
+    const double Xp = (up - T.cx) * T.g, Yp = (vp - T.cy) * T.g;
+    const double fr = 4.0 * T.R * T.R, r2 = Xp * Xp + Yp * Yp;
+    const double inv_den = 1.0 / (fr + r2);
+    G.up = up;
+    G.vp = vp;
+    G.hp = hp;
+    G.nhat[0] = 4.0 * T.R * Xp * inv_den;
+    G.nhat[1] = 4.0 * T.R * Yp * inv_den;
+    G.nhat[2] = (fr - r2) * inv_den;
+    G.sin_e = G.nhat[0] * T.sx + G.nhat[1] * T.sy + G.nhat[2] * T.sz;
+    G.rho = T.R + hp;
+    G.inv_rho = 1.0 / G.rho;
+    // a0 = rho (1 + n_z) = rho 2 fr / (fr + r2)
+    G.inv_a0 = G.inv_rho * (fr + r2) / (2.0 * fr);
+    const double k = 2.0 * T.R / T.g;
+    G.Au = T.delta * k * T.sx * G.inv_a0;
+    G.Av = T.delta * k * T.sy * G.inv_a0;
+    G.Bu = k * G.rho * G.nhat[0] * G.inv_a0 * G.inv_a0;
+    G.Bv = k * G.rho * G.nhat[1] * G.inv_a0 * G.inv_a0;
+    G.b = 0.0;
+    const double cx = G.nhat[1] * T.sz - G.nhat[2] * T.sy;
+    const double cy = G.nhat[2] * T.sx - G.nhat[0] * T.sz;
+    const double cz = G.nhat[0] * T.sy - G.nhat[1] * T.sx;
+    const double cn = sqrt(cx * cx + cy * cy + cz * cz);
+    G.nz_cross = cn > 0.0 ? fabs(cz) / cn : 0.0;
+}
+
+// Either mapping; `stereo` is a compile-time constant in the forward kernels
+// (one mapping per instance) and T.proj != 0 in the backward kernel.
+__device__ __forceinline__ void geom64_any(const Tile& T, double up, double vp, double hp,
+                                           Geom64& G, bool stereo) {
+    if (!stereo)
+        geom64(T, up, vp, hp, G);
+    else
+        geom64_stereo(T, up, vp, hp, G);
+}
+
+// FP64 rise |p + t s| - |p| without cancellation
+__device__ __forceinline__ double rise64(const Geom64& G, double t) {
+    const double w = t * (2.0 * G.rho * G.sin_e + t);
+    return w / (G.rho + sqrt(G.rho * G.rho + w));
+}
+
+// FP64 texel position of the point of the ray at distance t (either mapping)
+__device__ __forceinline__ void pos64(const Tile& T, const Geom64& G, double jd, double t,
+                                      double& U, double& V, bool stereo) {
+    if (!stereo) {
+        const double tau = jd / (1.0 + G.b * jd);
+        U = G.up + G.Au * tau;
+        V = G.vp + G.Av * tau;
+    } else {
+        const double w = rise64(G, t) + t * T.sz;
+        const double den = 1.0 + w * G.inv_a0;
+        U = G.up + (G.Au * jd - G.Bu * w) / den;
+        V = G.vp + (G.Av * jd - G.Bv * w) / den;
+    }
+}
+
 __device__ __forceinline__ double cos_elev(const Geom64& G) {
     return sqrt(fmax(0.0, 1.0 - G.sin_e * G.sin_e));
 }
@@ -220,6 +293,126 @@ __device__ __forceinline__ void sample_range(const Tile& T, const Geom64& G, int
     j_hi = (int32_t)fmin((double)T.J, floor(jh));
 }
 
+// (stereographic tiles only)
+__device__ __forceinline__ bool inside64(const Tile& T, const Geom64& G, int32_t j) {
+    double U, V;
+    pos64(T, G, (double)j, (double)j * T.delta, U, V, true);
+    return U >= 0.0 && U <= (double)(T.nx - 1) && V >= 0.0 && V <= (double)(T.ny - 1);
+}
+
+// Polar stereographic usable range: the first run of in-tile samples.  The
+// ray's directions sweep a great circle (plane N . n = 0, N = p x s); the
+// preimage of a tile edge X = X_B is the small circle E . n = e0 with
+// E = (2R, 0, -X_B), e0 = X_B (likewise for Y).  Their intersections give the
+// crossing points exactly (a quadratic), each mapped back to its ray distance
+// t = -((p x n) . (s x n)) / |s x n|^2; the run is bounded by the first
+// crossings, then its end samples are confirmed with the FP64 position.
+__device__ __forceinline__ void sample_range_stereo(const Tile& T, const Geom64& G,
+                                                    int32_t& j_lo, int32_t& j_hi) {
+    const double p[3] = { G.rho * G.nhat[0], G.rho * G.nhat[1], G.rho * G.nhat[2] };
+    const double sv[3] = { T.sx, T.sy, T.sz };
+    const double N[3] = { p[1] * sv[2] - p[2] * sv[1], p[2] * sv[0] - p[0] * sv[2],
+                          p[0] * sv[1] - p[1] * sv[0] };
+    const double Xlo = (0.0 - T.cx) * T.g, Xhi = ((double)(T.nx - 1) - T.cx) * T.g;
+    const double Ylo = (0.0 - T.cy) * T.g, Yhi = ((double)(T.ny - 1) - T.cy) * T.g;
+    double tc[8];
+    int nc = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const bool xedge = e < 2;
+        const double B = xedge ? (e == 0 ? Xlo : Xhi) : (e == 2 ? Ylo : Yhi);
+        const double E[3] = { xedge ? 2.0 * T.R : 0.0, xedge ? 0.0 : 2.0 * T.R, -B };
+        const double e0 = B;
+        const double d[3] = { N[1] * E[2] - N[2] * E[1], N[2] * E[0] - N[0] * E[2],
+                              N[0] * E[1] - N[1] * E[0] };
+        const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (!(dd > 0.0)) continue;
+        const double NN = N[0] * N[0] + N[1] * N[1] + N[2] * N[2];
+        const double NE = N[0] * E[0] + N[1] * E[1] + N[2] * E[2];
+        double x0[3];
+        for (int i = 0; i < 3; ++i) x0[i] = e0 * (NN * E[i] - NE * N[i]) / dd;
+        const double bq = x0[0] * d[0] + x0[1] * d[1] + x0[2] * d[2];
+        const double cq = x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2] - 1.0;
+        const double disc = bq * bq - dd * cq;
+        if (!(disc >= 0.0)) continue;
+        const double sq = sqrt(disc);
+        for (int k = 0; k < 2; ++k) {
+            const double lam = (-bq + (k ? sq : -sq)) / dd;
+            const double n[3] = { x0[0] + lam * d[0], x0[1] + lam * d[1], x0[2] + lam * d[2] };
+            if (!(1.0 + n[2] > 0.0)) continue;
+            const double other = 2.0 * T.R * (xedge ? n[1] : n[0]) / (1.0 + n[2]);
+            const double olo = xedge ? Ylo : Xlo, ohi = xedge ? Yhi : Xhi;
+            if (other < olo || other > ohi) continue;
+            const double pn[3] = { p[1] * n[2] - p[2] * n[1], p[2] * n[0] - p[0] * n[2],
+                                   p[0] * n[1] - p[1] * n[0] };
+            const double sn[3] = { sv[1] * n[2] - sv[2] * n[1], sv[2] * n[0] - sv[0] * n[2],
+                                   sv[0] * n[1] - sv[1] * n[0] };
+            const double s2 = sn[0] * sn[0] + sn[1] * sn[1] + sn[2] * sn[2];
+            if (!(s2 > 0.0)) continue;
+            const double t = -(pn[0] * sn[0] + pn[1] * sn[1] + pn[2] * sn[2]) / s2;
+            const double lam2 = (p[0] + t * sv[0]) * n[0] + (p[1] + t * sv[1]) * n[1] +
+                                (p[2] + t * sv[2]) * n[2];
+            if (t > 0.0 && lam2 > 0.0 && nc < 8) tc[nc++] = t;
+        }
+    }
+    // sort the crossing distances (at most 8)
+    for (int i = 1; i < nc; ++i)
+        for (int k = i; k > 0 && tc[k] < tc[k - 1]; --k) {
+            const double tmp = tc[k];
+            tc[k] = tc[k - 1];
+            tc[k - 1] = tmp;
+        }
+    // Between consecutive crossings the in/out status is constant (tested at the
+    // interval's midpoint).  The run starts in the first inside interval that
+    // holds a sample and extends over later inside intervals until an outside
+    // interval that holds a sample (an excursion between two samples does not
+    // split the run: both samples are in the tile).
+    const double tmax = (double)T.J * T.delta;
+    int32_t run_lo = -1, run_hi = -1;
+    double lo_t = 0.0;
+    for (int i = 0; i <= nc; ++i) {
+        const double hi_t = i < nc ? fmin(tc[i], tmax) : tmax;
+        if (hi_t > lo_t) {
+            const int32_t lo = (int32_t)fmax(1.0, ceil(lo_t / T.delta));
+            const int32_t hi = (int32_t)fmin((double)T.J, floor(hi_t / T.delta));
+            const double tm = 0.5 * (lo_t + hi_t);
+            double U, V;
+            pos64(T, G, tm / T.delta, tm, U, V, true);
+            const bool in = U >= 0.0 && U <= (double)(T.nx - 1) && V >= 0.0 &&
+                            V <= (double)(T.ny - 1);
+            if (lo <= hi) {
+                if (in) {
+                    if (run_lo < 0) run_lo = lo;
+                    run_hi = hi;
+                } else if (run_lo >= 0) {
+                    break;
+                }
+            }
+        }
+        if (hi_t >= tmax) break;
+        lo_t = hi_t;
+    }
+    if (run_lo < 0) {
+        j_lo = 1;
+        j_hi = 0;
+        return;
+    }
+    // confirm the ends with the FP64 positions (a crossing within rounding of a sample)
+    int32_t lo = run_lo, hi = run_hi;
+    if (!inside64(T, G, lo) && lo < hi) ++lo;
+    if (lo > 1 && inside64(T, G, lo - 1)) --lo;
+    if (!inside64(T, G, hi) && hi > lo) --hi;
+    if (hi < T.J && inside64(T, G, hi + 1)) ++hi;
+    if (!inside64(T, G, lo)) {
+        j_lo = 1;
+        j_hi = 0;
+        return;
+    }
+    j_lo = lo;
+    j_hi = hi;
+}
+
+template <bool kStereo>
 __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double href,
                                           float span, RayF& r) {
     double iu = floor(G.up), iv = floor(G.vp);
@@ -237,11 +430,25 @@ __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double
     r.href = (float)href;
     r.tv = G.sin_e < 0.0 ? (float)(-G.rho * G.sin_e) : -1.0f;
     r.guard0 = fabsf(r.X) + span;
-    sample_range(T, G, r.j_lo, r.j_hi);
+    if (!kStereo) {
+        sample_range(T, G, r.j_lo, r.j_hi);
+        r.bu = r.bv = r.inv8r = 0.0f;
+    } else {
+        sample_range_stereo(T, G, r.j_lo, r.j_hi);
+        r.b = (float)G.inv_a0;
+        r.bu = (float)G.Bu;
+        r.bv = (float)G.Bv;
+        r.inv8r = (float)(G.nz_cross * T.g / (16.0 * T.R));
+    }
     // float32 block-end positions u0 + a*tau err by <= ulp(coordinate) plus
     // ~3 ulp of a*tau; the margin takes 4x that, plus 1e-3 texel
     float amax = fmaxf(fabsf((float)G.Au), fabsf((float)G.Av));
     r.pos_eps = 1e-3f + 5e-7f * (float)(T.nx + T.ny) + 8e-7f * amax * (float)max(r.j_hi, 1);
+    if (kStereo) {
+        // the stereographic end positions also carry w * B with |w| <= 2 t
+        const float bmax = fmaxf(fabsf(r.bu), fabsf(r.bv));
+        r.pos_eps += 8e-7f * bmax * 2.0f * (float)((double)max(r.j_hi, 1) * T.delta);
+    }
 }
 
 // ------------------------------------------------------------ float32 leaf
@@ -263,15 +470,18 @@ __device__ __forceinline__ float corr_of(const RayF& r, float jf) {
 }
 
 // Texel coordinate of sample j along one axis: integer part exact, fraction
-// accurate to ~1e-7 texel.  Base clamped to [0, n-2] (the fraction absorbs it).
-template <bool kGrid>
+// accurate to ~1e-7 texel.  The offset from the origin is j*a (a = a_hi + a_lo,
+// j*a_hi exact) minus a small correction that carries the curvature of the
+// mapping: a * corr (gnomonic, corr = j - j/(1 + b j)) or corr itself
+// (stereographic, in texels).  Base clamped to [0, n-2] (the fraction absorbs it).
+template <bool kGrid, bool kStereo>
 __device__ __forceinline__ Pos axis_pos(int32_t i0, float u0, float a_hi, float a_lo,
                                         float corr, float jf, int32_t n) {
     float p = __fmul_rn(jf, a_hi);       // exact: a_hi has <= 8 significant bits
     float kp = floorf(p);
     float fp = __fsub_rn(p, kp);         // exact
-    float a = __fadd_rn(a_hi, a_lo);
-    float tail = __fmaf_rn(jf, a_lo, -__fmul_rn(a, corr));
+    float tail = kStereo ? __fmaf_rn(jf, a_lo, -corr)
+                         : __fmaf_rn(jf, a_lo, -__fmul_rn(__fadd_rn(a_hi, a_lo), corr));
     float s = kGrid ? __fadd_rn(fp, tail)
                     : __fadd_rn(__fadd_rn(__fsub_rn(u0, (float)i0), fp), tail);
     float fs = floorf(s);
@@ -323,6 +533,23 @@ __device__ __forceinline__ float bilerp_rn(float d00, float d10, float d01, floa
     return __fmaf_rn(fv, __fsub_rn(bot, top), top);
 }
 
+// Corrections of sample j's offset along u and v (see axis_pos):
+//   gnomonic:      j - j/(1 + b j) for both axes (axis_pos scales it by a)
+//   stereographic: w (B + j a / a0) / (1 + w / a0) texels, w = rise(t_j) + t_j s_z
+template <bool kStereo>
+__device__ __forceinline__ void axis_corr(const Tile& T, const RayF& r, float jf, float t,
+                                          float rise, float& cu, float& cv) {
+    if (!kStereo) {
+        cu = cv = corr_of(r, jf);
+    } else {
+        const float au = __fadd_rn(r.au_hi, r.au_lo), av = __fadd_rn(r.av_hi, r.av_lo);
+        const float w = __fadd_rn(rise, __fmul_rn(t, T.sz_f));
+        const float q = __fdividef(w, __fmaf_rn(w, r.b, 1.0f));   // r.b = 1/a0
+        cu = __fmul_rn(q, __fmaf_rn(__fmul_rn(jf, au), r.b, r.bu));
+        cv = __fmul_rn(q, __fmaf_rn(__fmul_rn(jf, av), r.b, r.bv));
+    }
+}
+
 // 1/t_j: delta^-1 times the hardware reciprocal of j (deterministic, <= 2 ulp)
 __device__ __forceinline__ float inv_t(const Tile& T, float jf) {
     return __fmul_rn(T.inv_delta_f, rcp_approx(jf));
@@ -336,30 +563,43 @@ __device__ __forceinline__ const float* cell_ptr(const float* base, uint32_t pit
 
 // Cost of sample j (float32); the uniform kernel's sample value.  probe() with
 // leaf == true returns the same bits.
-template <bool kGrid, bool kPoly>
+template <bool kGrid, bool kPoly, bool kStereo>
 __device__ __forceinline__ float leaf_cost(const Tile& T, const RayF& r, int32_t j,
                                            float& rise) {
     const float jf = (float)j;
-    const float corr = corr_of(r, jf);
-    const Pos pu = axis_pos<kGrid>(r.iu0, r.u0, r.au_hi, r.au_lo, corr, jf, T.nx);
-    const Pos pv = axis_pos<kGrid>(r.iv0, r.v0, r.av_hi, r.av_lo, corr, jf, T.ny);
     const float t = __fmul_rn(jf, T.delta_f);
-    rise = rise_of<kPoly>(r, t);
+    const float rise_s = kStereo ? rise_of<kPoly>(r, t) : 0.0f;
+    float cu, cv;
+    axis_corr<kStereo>(T, r, jf, t, rise_s, cu, cv);
+    const Pos pu = axis_pos<kGrid, kStereo>(r.iu0, r.u0, r.au_hi, r.au_lo, cu, jf, T.nx);
+    const Pos pv = axis_pos<kGrid, kStereo>(r.iv0, r.v0, r.av_hi, r.av_lo, cv, jf, T.ny);
     const uint32_t pitch = (uint32_t)T.pitch;
     const float* p = cell_ptr(T.h, pitch, pu.i, pv.i);
     const float d00 = __fsub_rn(__ldg(p), r.href), d10 = __fsub_rn(__ldg(p + 1), r.href);
     const float d01 = __fsub_rn(__ldg(p + pitch), r.href);
     const float d11 = __fsub_rn(__ldg(p + pitch + 1), r.href);
+    rise = kStereo ? rise_s : rise_of<kPoly>(r, t);
     const float hb = bilerp_rn(d00, d10, d01, d11, pu.f, pv.f);
     const float h = kGrid ? rise : __fadd_rn(r.X, rise);
     return __fmul_rn(__fsub_rn(h, hb), inv_t(T, jf));
 }
 
-// float32 texel position of sample j for block footprints (error <= pos_eps)
-__device__ __forceinline__ void block_end(const RayF& r, float jf, float& u, float& v) {
-    float tau = __fdividef(jf, __fmaf_rn(jf, r.b, 1.0f));
-    u = __fmaf_rn(__fadd_rn(r.au_hi, r.au_lo), tau, r.u0);
-    v = __fmaf_rn(__fadd_rn(r.av_hi, r.av_lo), tau, r.v0);
+// float32 texel position of sample j for block footprints (error <= pos_eps);
+// rise = rise(t_j) (used by the stereographic mapping only)
+template <bool kStereo>
+__device__ __forceinline__ void block_end(const Tile& T, const RayF& r, float jf, float t,
+                                          float rise, float& u, float& v) {
+    const float au = __fadd_rn(r.au_hi, r.au_lo), av = __fadd_rn(r.av_hi, r.av_lo);
+    if (!kStereo) {
+        float tau = __fdividef(jf, __fmaf_rn(jf, r.b, 1.0f));
+        u = __fmaf_rn(au, tau, r.u0);
+        v = __fmaf_rn(av, tau, r.v0);
+    } else {
+        const float w = __fadd_rn(rise, __fmul_rn(t, T.sz_f));
+        const float id = __fdividef(1.0f, __fmaf_rn(w, r.b, 1.0f));
+        u = __fmaf_rn(__fmaf_rn(jf, au, -__fmul_rn(w, r.bu)), id, r.u0);
+        v = __fmaf_rn(__fmaf_rn(jf, av, -__fmul_rn(w, r.bv)), id, r.v0);
+    }
 }
 
 // Levels of the maximum mipmap as a kernel sees them (shared memory copy).
@@ -379,23 +619,33 @@ struct LevelTab {
 //    widened by pos_eps); the guard 2^-19 (|X| + |rise| + |M - h_ref| + span)
 //    covers every float32 rounding of the leaf and of the bound, so no sample
 //    that could win is skipped.
-template <bool kGrid, bool kPoly>
+template <bool kGrid, bool kPoly, bool kStereo>
 __device__ __forceinline__ float probe(const Tile& T, const LevelTab& L, int32_t levels,
                                        const RayF& r, int32_t ja, int32_t jb, bool leaf) {
     const float fa = (float)ja, fb = (float)jb;
+    // stereographic positions need the rise at both ends first
+    const float sa = kStereo ? __fmul_rn(fa, T.delta_f) : 0.0f;
+    const float sb = kStereo ? __fmul_rn(fb, T.delta_f) : 0.0f;
+    const float rise_a = kStereo ? rise_of<kPoly>(r, sa) : 0.0f;
     // leaf position (the sample's bilinear cell)
-    const float ca = corr_of(r, fa);
-    const Pos ua = axis_pos<kGrid>(r.iu0, r.u0, r.au_hi, r.au_lo, ca, fa, T.nx);
-    const Pos va = axis_pos<kGrid>(r.iv0, r.v0, r.av_hi, r.av_lo, ca, fa, T.ny);
-    // block footprint box from both ends
+    float cu, cv;
+    axis_corr<kStereo>(T, r, fa, sa, rise_a, cu, cv);
+    const Pos ua = axis_pos<kGrid, kStereo>(r.iu0, r.u0, r.au_hi, r.au_lo, cu, fa, T.nx);
+    const Pos va = axis_pos<kGrid, kStereo>(r.iv0, r.v0, r.av_hi, r.av_lo, cv, fa, T.ny);
+    // block footprint box from both ends (stereographic: plus the arc's sagitta)
     float xa, ya, xb, yb;
-    block_end(r, fa, xa, ya);
-    block_end(r, fb, xb, yb);
-    const float e = r.pos_eps;
+    block_end<kStereo>(T, r, fa, sa, rise_a, xa, ya);
+    block_end<kStereo>(T, r, fb, sb, kStereo ? rise_of<kPoly>(r, sb) : 0.0f, xb, yb);
+    float e = r.pos_eps;
+    if (kStereo) {
+        const float dx = xb - xa, dy = yb - ya;
+        e += (dx * dx + dy * dy) * r.inv8r;
+    }
+    // clamped before the +1, so no conversion result can overflow
     int32_t x0 = max(__float2int_rd(fminf(xa, xb) - e), 0);
-    int32_t x1 = min(__float2int_rd(fmaxf(xa, xb) + e) + 1, T.nx - 1);
+    int32_t x1 = min(__float2int_rd(fmaxf(xa, xb) + e), T.nx - 2) + 1;
     int32_t y0 = max(__float2int_rd(fminf(ya, yb) - e), 0);
-    int32_t y1 = min(__float2int_rd(fmaxf(ya, yb) + e) + 1, T.ny - 1);
+    int32_t y1 = min(__float2int_rd(fmaxf(ya, yb) + e), T.ny - 2) + 1;
     const int32_t ext = max(x1 - x0, y1 - y0);
     int32_t m = ext <= 1 ? 0 : 31 - __clz(ext);
     m += (((x1 >> m) - (x0 >> m)) > 1 || ((y1 >> m) - (y0 >> m)) > 1) ? 1 : 0;
@@ -415,7 +665,7 @@ __device__ __forceinline__ float probe(const Tile& T, const LevelTab& L, int32_t
     const float d11 = __fsub_rn(__ldg(p + dy + dx), r.href);
     const float ta = __fmul_rn(fa, T.delta_f), tb = __fmul_rn(fb, T.delta_f);
     const float tstar = (leaf || !(r.tv > ta)) ? ta : fminf(r.tv, tb);
-    const float rise = rise_of<kPoly>(r, tstar);
+    const float rise = rise_of<kPoly>(r, tstar);             // = rise(ta) for a leaf
     const float V = leaf ? bilerp_rn(d00, d10, d01, d11, ua.f, va.f)
                          : fmaxf(fmaxf(d00, d10), fmaxf(d01, d11));
     const float h = kGrid ? rise : __fadd_rn(r.X, rise);
@@ -428,19 +678,18 @@ __device__ __forceinline__ float probe(const Tile& T, const LevelTab& L, int32_t
 
 // ------------------------------------------------------ FP64 re-evaluation
 __device__ __forceinline__ double leaf_cost64(const Tile& T, const Geom64& G, int32_t j,
-                                              double* U = nullptr, double* V = nullptr) {
-    double jd = (double)j;
-    double tau = jd / (1.0 + G.b * jd);
-    double u = G.up + G.Au * tau, v = G.vp + G.Av * tau;
+                                              bool stereo, double* U = nullptr,
+                                              double* V = nullptr) {
+    const double jd = (double)j;
+    const double t = jd * T.delta;
+    double u, v;
+    pos64(T, G, jd, t, u, v, stereo);
     if (U) *U = u;
     if (V) *V = v;
     int32_t i0, j0;
     double w[4];
-    double hb = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, u, v, &i0, &j0, w);
-    double t = jd * T.delta;
-    double wq = t * (2.0 * G.rho * G.sin_e + t);
-    double rise = wq / (G.rho + sqrt(G.rho * G.rho + wq));
-    return ((G.hp - hb) + rise) / t;
+    const double hb = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, u, v, &i0, &j0, w);
+    return ((G.hp - hb) + rise64(G, t)) / t;
 }
 
 __device__ __forceinline__ double disc_light64(double d) {

@@ -1,0 +1,221 @@
+// Forward kernels (exact max-mip descent and uniform stepping), templated on
+// the tile mapping; fwd_gnomonic.cu and fwd_stereo.cu each instantiate one
+// mapping so the two compile in parallel.
+//
+// Work decomposition: one thread walks one shadow ray at a time; each block
+// owns a contiguous range of ray ids (grid mode: row-major texels, so a warp's
+// rays are neighbours whose samples touch neighbouring texels) and its lanes
+// draw rays from that range as they finish.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ss_launch.h"
+#include "ss_walk.cuh"
+
+namespace ss {
+
+// Minimum resident 256-thread blocks per SM for the forward kernels (caps
+// registers at 65536 / (256 * SS_FWD_MIN_BLOCKS)).
+#ifndef SS_FWD_MIN_BLOCKS
+#define SS_FWD_MIN_BLOCKS 4
+#endif
+
+// Scheduling shared by both forward kernels.  Block b owns rays
+// [b*rays_per_block, ...) (the grid oversubscribes the SMs so the hardware
+// block scheduler balances them).  Each lane walks one ray.  A lane whose ray
+// is finished keeps its result in registers and waits; once at least
+// refill_min lanes of the warp are waiting (or all are), the warp services
+// them together: finished rays are written, and the waiting lanes draw the
+// next rays of the block pool (one shared-memory atomic per warp).
+__device__ __forceinline__ ChunkRange block_pool(const FwdArgs& a, int32_t* s_next) {
+    if (threadIdx.x == 0) *s_next = 0;
+    return chunk_range(blockIdx.x, ray_count(a.T, a.R), a.T.nx, a.T.ny, (int32_t)a.rays_per_block,
+                       a.R.mode == 0 ? a.tile_w : 0);
+}
+
+// Draw rays for this warp's lanes with r < 0; returns the new local index or -1.
+__device__ __forceinline__ int32_t draw(const ChunkRange& P, int32_t* s_next, int32_t r,
+                                        bool& open) {
+    const unsigned idle = __ballot_sync(kFull, r < 0);
+    const int nidle = __popc(idle);
+    int base = 0;
+    if ((threadIdx.x & 31) == 0 && nidle > 0) base = atomicAdd(s_next, nidle);
+    base = __shfl_sync(kFull, base, 0);
+    if (base + nidle >= P.cnt) open = false;
+    if (r >= 0) return r;
+    const int my = base + __popc(idle & lanemask_lt());
+    return my < P.cnt ? my : -1;
+}
+
+// ---------------------------------------------------------------- descent
+// Each loop iteration is one probe of the exact descent (walk_step) per
+// walking lane.
+template <bool kCount, bool kGrid, bool kPoly, bool kLight, bool kStereo>
+__global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(const FwdArgs a) {
+    __shared__ LevelTab s_lev;
+    __shared__ int32_t s_next;
+    if (threadIdx.x < kMaxLevels) {
+        s_lev.ptr[threadIdx.x] = a.P.ptr[threadIdx.x];
+        s_lev.pitch[threadIdx.x] = (uint32_t)a.P.pitch[threadIdx.x];
+    }
+    const ChunkRange P = block_pool(a, &s_next);
+    __syncthreads();
+    const float span = a.stats[0] - a.stats[1];
+    const int32_t kleaf = a.kleaf, levels = a.P.levels;
+
+    int32_t r = -1;
+    bool done = false, open = true;
+    RayF rf;
+    Walk w;
+    w.best = INFINITY;
+    w.bestj = -1;
+    while (true) {
+        unsigned act = __ballot_sync(kFull, r >= 0 && !done);
+        if (act == 0 || (open && __popc(~act) >= a.refill_min)) {
+            if (done) {
+                finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj, w.nb, w.nl);
+                r = -1;
+                done = false;
+            }
+            if (open) {
+                const int32_t nr = draw(P, &s_next, r, open);
+                if (nr >= 0 && r < 0) {
+                    r = nr;
+                    setup_ray<kGrid, kLight, kStereo>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
+                    walk_begin<kLight>(w, rf, kleaf);
+                    if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
+                        finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj, 0, 0);
+                        r = -1;
+                    }
+                }
+            }
+            act = __ballot_sync(kFull, r >= 0 && !done);
+            if (act == 0) {
+                if (!open) break;
+                continue;
+            }
+        }
+        if (r < 0 || done) continue;
+        done = walk_step<kCount, kGrid, kPoly, kLight, kStereo>(a.T, s_lev, levels, kleaf, rf, w);
+    }
+}
+
+// ---------------------------------------------------------------- uniform
+// Every usable sample in order, same scheduling as the descent.  Early exit
+// (exact): with H(t) = h_p + rise(t) convex and H(0) = h_p <= max h,
+// g(t) = (H(t) - max h - G)/t is non-decreasing and bounds every later
+// sample's cost from below; once g(t_j) >= best no later sample can win.
+// G = 3 guards covers the float32 rounding of both sides.
+template <bool kCount, bool kGrid, bool kPoly, bool kLight, bool kStereo>
+__global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) uniform_forward_kernel(const FwdArgs a) {
+    __shared__ int32_t s_next;
+    const ChunkRange P = block_pool(a, &s_next);
+    __syncthreads();
+    const float hmax = a.stats[0];
+    const float span = a.stats[0] - a.stats[1];
+    const bool allow_exit = !(a.flags & 0x2u);
+
+    int32_t r = -1;
+    bool done = false, open = true;
+    RayF rf;
+    float best = INFINITY, hmax_rel = 0.0f, G = 0.0f;
+    int32_t bestj = -1, nl = 0, j = 0;
+    bool exit_ok = false;
+    while (true) {
+        unsigned act = __ballot_sync(kFull, r >= 0 && !done);
+        if (act == 0 || (open && __popc(~act) >= a.refill_min)) {
+            if (done) {
+                finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), best, bestj, 0, nl);
+                r = -1;
+                done = false;
+            }
+            if (open) {
+                const int32_t nr = draw(P, &s_next, r, open);
+                if (nr >= 0 && r < 0) {
+                    r = nr;
+                    setup_ray<kGrid, kLight, kStereo>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
+                    best = kLight ? rf.c_sat : INFINITY;
+                    bestj = -1;
+                    nl = 0;
+                    j = rf.j_lo;
+                    hmax_rel = hmax - rf.href;
+                    exit_ok = allow_exit && (rf.X <= hmax_rel);
+                    const float tJ = (float)rf.j_hi * a.T.delta_f;
+                    const float rb = fmaxf(rise_bound(rf, tJ),
+                                           0.5f * rf.B * rf.B * rf.inv_2rho);
+                    G = 3.0f * kGuardRel * (rf.guard0 + fabsf(hmax_rel) + rb);
+                    if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
+                        finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), best, bestj, 0, 0);
+                        r = -1;
+                    }
+                }
+            }
+            act = __ballot_sync(kFull, r >= 0 && !done);
+            if (act == 0) {
+                if (!open) break;
+                continue;
+            }
+        }
+        if (r < 0 || done) continue;
+        float rise;
+        const float c = leaf_cost<kGrid, kPoly, kStereo>(a.T, rf, j, rise);
+        if (kCount) ++nl;
+        const bool improve = c < best;
+        best = improve ? c : best;
+        bestj = improve ? j : bestj;
+        bool stop = (j >= rf.j_hi);
+        if (exit_ok && (j & 3) == 0) {
+            const float t = __fmul_rn((float)j, a.T.delta_f);
+            const float h = kGrid ? rise : rf.X + rise;
+            stop = stop || ((h - hmax_rel) - G) / t >= best;
+        }
+        ++j;
+        done = kLight ? (stop || best <= -rf.c_sat) : stop;
+    }
+}
+
+static int pool_grid(const FwdArgs& a) {
+    const int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
+    return (int)chunk_count(n, a.T.nx, a.T.ny, (int32_t)a.rays_per_block,
+                            a.R.mode == 0 ? a.tile_w : 0);
+}
+
+#define SS_FWD_CASE(C, G, P, L) \
+    case ((C) << 3) | ((G) << 2) | ((P) << 1) | (L): return Launch<C, G, P, L, kStereo>::go(a, grid, block, s);
+
+// runtime flags -> the kernel instance (counters, grid mode, rise series, light-only)
+template <bool kStereo, template <bool, bool, bool, bool, bool> class Launch>
+static cudaError_t dispatch(const FwdArgs& a, int block, cudaStream_t s) {
+    const int idx = ((a.O.counters != nullptr) << 3) | ((a.R.mode == 0) << 2) | ((a.poly != 0) << 1) |
+                    ((a.flags & 0x4u) ? 1 : 0);
+    const int grid = pool_grid(a);
+    switch (idx) {
+        SS_FWD_CASE(0, 0, 0, 0) SS_FWD_CASE(0, 0, 0, 1) SS_FWD_CASE(0, 0, 1, 0) SS_FWD_CASE(0, 0, 1, 1)
+        SS_FWD_CASE(0, 1, 0, 0) SS_FWD_CASE(0, 1, 0, 1) SS_FWD_CASE(0, 1, 1, 0) SS_FWD_CASE(0, 1, 1, 1)
+        SS_FWD_CASE(1, 0, 0, 0) SS_FWD_CASE(1, 0, 0, 1) SS_FWD_CASE(1, 0, 1, 0) SS_FWD_CASE(1, 0, 1, 1)
+        SS_FWD_CASE(1, 1, 0, 0) SS_FWD_CASE(1, 1, 0, 1) SS_FWD_CASE(1, 1, 1, 0) SS_FWD_CASE(1, 1, 1, 1)
+    }
+    return cudaErrorInvalidValue;
+}
+#undef SS_FWD_CASE
+
+template <bool C, bool G, bool P, bool L, bool S>
+struct DpLaunch {
+    static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
+        dp_forward_kernel<C, G, P, L, S><<<grid, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+template <bool C, bool G, bool P, bool L, bool S>
+struct UniLaunch {
+    static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
+        uniform_forward_kernel<C, G, P, L, S><<<grid, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace ss

@@ -21,7 +21,8 @@ __device__ __forceinline__ int64_t ray_count(const Tile& T, const Rays& R) {
 
 // cos(eps_p) of ray r's origin in float32 (relative error ~1e-7), enough to
 // decide whether its light is saturated.
-__device__ __forceinline__ float cos_elev_f32(const Tile& T, const Rays& R, int64_t r) {
+__device__ __forceinline__ float cos_elev_f32(const Tile& T, const Rays& R, int64_t r,
+                                              bool stereo) {
     float u, v;
     if (R.mode == 0) {
         const int64_t vv = r / T.nx;
@@ -33,14 +34,22 @@ __device__ __forceinline__ float cos_elev_f32(const Tile& T, const Rays& R, int6
     }
     const float g = (float)T.g, Rs = (float)T.R;
     const float X = (u - (float)T.cx) * g, Y = (v - (float)T.cy) * g;
-    const float se = (X * (float)T.sx + Y * (float)T.sy + Rs * (float)T.sz) *
-                     rsqrtf(X * X + Y * Y + Rs * Rs);
+    float se;
+    if (!stereo) {
+        se = (X * (float)T.sx + Y * (float)T.sy + Rs * (float)T.sz) *
+             rsqrtf(X * X + Y * Y + Rs * Rs);
+    } else {   // n = (2x, 2y, 1 - x^2 - y^2) / (1 + x^2 + y^2), (x, y) = (X, Y) / 2R
+        const float k = 0.5f / Rs, x = X * k, y = Y * k, q = x * x + y * y;
+        se = (2.0f * x * (float)T.sx + 2.0f * y * (float)T.sy + (1.0f - q) * (float)T.sz) /
+             (1.0f + q);
+    }
     return sqrtf(fmaxf(0.0f, 1.0f - se * se));
 }
 
 // Final value of one ray: re-evaluate the argmin sample in FP64 unless the
 // light is certainly saturated (|c*| cos(eps) >= 1.001 alpha), then the
 // disc-occlusion formula (Eq. discfrac).
+template <bool kStereo = false>
 __device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const Outputs& O,
                                            int64_t r, float best, int32_t bestj, int32_t nb,
                                            int32_t nl) {
@@ -48,7 +57,7 @@ __device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const O
     if (bestj < 0) {
         light = 1.0f;
         cost = INFINITY;
-    } else if (fabsf(best) * cos_elev_f32(T, R, r) >= 1.001f * T.alpha_f) {
+    } else if (fabsf(best) * cos_elev_f32(T, R, r, kStereo) >= 1.001f * T.alpha_f) {
         light = best > 0.0f ? 1.0f : 0.0f;
         cost = best;
     } else {
@@ -56,8 +65,8 @@ __device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const O
         int32_t oi0, oj0;
         ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
         Geom64 G;
-        geom64(T, up, vp, hp, G);
-        double c = leaf_cost64(T, G, bestj);
+        geom64_any(T, up, vp, hp, G, kStereo);
+        double c = leaf_cost64(T, G, bestj, kStereo);
         light = (float)disc_light64(c * cos_elev(G) / T.alpha);
         cost = (float)c;
     }
@@ -70,7 +79,7 @@ __device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const O
     }
 }
 
-template <bool kGrid, bool kLight = false>
+template <bool kGrid, bool kLight = false, bool kStereo = false>
 __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t r, float span,
                                           RayF& rf) {
     double up, vp, hp, href;
@@ -85,8 +94,8 @@ __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t 
         ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
     }
     Geom64 G;
-    geom64(T, up, vp, hp, G);
-    make_rayf(T, G, href, span, rf);
+    geom64_any(T, up, vp, hp, G, kStereo);
+    make_rayf<kStereo>(T, G, href, span, rf);
     if (kGrid) rf.X = 0.0f;
     if (kLight) {   // saturation threshold of the light (with a 0.2% margin)
         const float se = (float)G.sin_e;
@@ -177,7 +186,7 @@ __device__ __forceinline__ void walk_begin(Walk& w, const RayF& rf, int32_t klea
 // k = ctz(s0), the next block in near-to-far order, so samples are evaluated
 // in increasing j and a strict '<' keeps the smallest j among equal costs.
 // Blocks are clipped to [j_lo, j_hi].
-template <bool kCount, bool kGrid, bool kPoly, bool kLight = false>
+template <bool kCount, bool kGrid, bool kPoly, bool kLight = false, bool kStereo = false>
 __device__ __forceinline__ bool walk_step(const Tile& T, const LevelTab& L, int32_t levels,
                                           int32_t kleaf, const RayF& rf, Walk& w) {
     const bool leaf = (w.k == 0);
@@ -187,7 +196,7 @@ __device__ __forceinline__ bool walk_step(const Tile& T, const LevelTab& L, int3
     const bool valid = leaf ? (s1 >= rf.j_lo) : (ja <= jb);
     ja = valid ? ja : rf.j_lo;
     jb = valid ? jb : rf.j_lo;
-    const float v = probe<kGrid, kPoly>(T, L, levels, rf, ja, jb, leaf);
+    const float v = probe<kGrid, kPoly, kStereo>(T, L, levels, rf, ja, jb, leaf);
     const bool improve = valid && leaf && (v < w.best);
     w.best = improve ? v : w.best;
     w.bestj = improve ? ja : w.bestj;

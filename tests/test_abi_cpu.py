@@ -87,7 +87,6 @@ def _fwd(hf, sun, prm, rays, out, mip=FAKE):
     (lambda a: setattr(a[4], "argmin", None), 1),
     (lambda a: setattr(a[2], "flags", 1), 1),        # counters requested but NULL
     (lambda a: a.__setitem__(5, 0), 1),              # NULL mip
-    (lambda a: setattr(a[0], "projection", 1), 7),   # valid, not in this build's kernels
 ])
 def test_forward_rejects_bad_arguments(mutate, expect):
     args = list(_good()) + [FAKE]
@@ -108,7 +107,7 @@ def test_batch_entry_points_reject_bad_arguments():
     assert lib.ss_batch_submit(p_items, 0, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws, None) == 2
     assert lib.ss_batch_submit(p_items, 2, ctypes.byref(prm), None, ws, None) == 1
     assert lib.ss_batch_submit(p_items, 2, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws - 1, None) == 3
-    items[1].hf.projection = 1
+    items[1].hf.projection = 1   # batches take gnomonic tiles only
     assert lib.ss_batch_submit(p_items, 2, ctypes.byref(prm), ctypes.c_void_p(FAKE), ws, None) == 7
     items[1].hf.projection = 0
     items[1].out.light = None
