@@ -35,6 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "shadow rays/s (DP+maxmip vs uniform stepping, same GB300, <=1e-5 err); fwd+bwd rays/s"
 UNIT = "rays/s"
 CONFIG = "mid"
+# dram__bytes_read.sum + dram__bytes_write.sum of one dp_forward_kernel launch on
+# the 4096x4096 workload (ncu, one pass); to be re-taken whenever the kernel changes
+MID_DP_TRAFFIC_BYTES = 78025728 + 85690368
 
 
 def parse_args(argv=None):
@@ -263,8 +266,13 @@ def run_ours(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_fwd / fwd_s / 1e9
+    # DRAM bytes of one launch of this kernel, from an ncu capture of this exact
+    # workload (profiles/dp_forward_grid2048.md, "DRAM traffic at the bench size");
+    # reported only for the workload and kernel settings it was taken on
+    traffic = (MID_DP_TRAFFIC_BYTES if (nx, ny) == (4096, 4096) and args.leaf_level < 0
+               and args.block == 0 else None)
     out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                       "frac": achieved / peak, "traffic": None,
+                       "frac": achieved / peak, "traffic": traffic,
                        "kernel": "dp_forward_kernel",
                        "algorithmic_bytes": bytes_fwd,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800",
