@@ -8,6 +8,8 @@ and shares no source with it.
 * ``oracle.cref`` -- ctypes binding of ``shadow_oracle.c`` (C, FP64, OpenMP):
   brute force over every sample of every ray, the analytic gradient at the
   argmin, and the maximum mipmap.
+  ``view_oracle.c`` adds the first terrain hit of a camera's view rays (the
+  polar scene's ray origins).
 * ``oracle.mini`` -- an independent NumPy restatement for tiny inputs, used to
   cross-check the C code.
 
@@ -16,7 +18,7 @@ Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 differences, and the C-vs-NumPy cross-check); none is "parity unpinned".
 """
 from .cref import (build_oracle, disc_light, shadow, ray_costs, sin_elev, grad,
-                   maxmip, num_threads, library_path)
+                   maxmip, num_threads, library_path, view_hits)
 
 __all__ = ["build_oracle", "disc_light", "shadow", "ray_costs", "sin_elev", "grad",
-           "maxmip", "num_threads", "library_path"]
+           "maxmip", "num_threads", "library_path", "view_hits"]

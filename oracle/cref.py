@@ -1,6 +1,7 @@
-"""ctypes binding of the C oracle (``shadow_oracle.c``).  Test infrastructure only.
+"""ctypes binding of the C oracle (``shadow_oracle.c``, ``view_oracle.c``).
+Test infrastructure only.
 
-``build_oracle()`` compiles the C file with gcc (FP64, IEEE semantics: no
+``build_oracle()`` compiles the C files with gcc (FP64, IEEE semantics: no
 fast-math, no FMA contraction, so x86 and Arm hosts give the same bits).
 """
 from __future__ import annotations
@@ -13,7 +14,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "shadow_oracle.c")
+_SRCS = [os.path.join(_HERE, "shadow_oracle.c"), os.path.join(_HERE, "view_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -30,11 +31,11 @@ def build_oracle(force=False):
     """Compile the oracle shared library (idempotent)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -62,6 +63,9 @@ def _load():
                                     p, p, p, p]
             lib.or_maxmip.restype = i32
             lib.or_maxmip.argtypes = [p, i32, i32, i64, p]
+            lib.ov_view_hits.restype = None
+            lib.ov_view_hits.argtypes = [p, i32, i32, i64, d, d, i32, p, p, p, p, d, d, i32,
+                                         i32, d, d, i64, p, p, p]
             lib.or_num_threads.restype = i32
             lib.or_num_threads.argtypes = []
             _lib = lib
@@ -182,3 +186,25 @@ def maxmip(h):
         levels.append(out[off:off + w * hh].reshape(hh, w).copy())
         off += w * hh
     return levels
+
+
+def view_hits(h, g, radius, cam, pixels, proj="polar_stereo"):
+    """First terrain hit of the view rays of the given pixels (indices into the
+    cam["width"] x cam["height"] frame, row-major): float64 arrays (u, v) of the
+    hit's texel coordinates, NaN where the pixel's ray hits nothing in the tile.
+    ``cam`` holds pos, forward, right, up, tan_x, tan_y, width, height, step_m,
+    max_dist_m (see ``workloads.camera``)."""
+    lib = _load()
+    h64 = _heights(h)
+    ny, nx = h64.shape
+    px = np.ascontiguousarray(pixels, dtype=np.int64)
+    u = np.empty(px.size, np.float64)
+    v = np.empty(px.size, np.float64)
+    vec = {k: np.ascontiguousarray(cam[k], dtype=np.float64) for k in
+           ("pos", "forward", "right", "up")}
+    lib.ov_view_hits(_ptr(h64), nx, ny, nx, float(g), float(radius), PROJ[proj],
+                     _ptr(vec["pos"]), _ptr(vec["forward"]), _ptr(vec["right"]), _ptr(vec["up"]),
+                     float(cam["tan_x"]), float(cam["tan_y"]), int(cam["width"]),
+                     int(cam["height"]), float(cam["step_m"]), float(cam["max_dist_m"]),
+                     px.size, _ptr(px), _ptr(u), _ptr(v))
+    return u, v

@@ -111,3 +111,37 @@ def bump_target(h, g, seed, n_bumps=64, sigma=50.0, amp=30.0):
         s = rng.choice([-1.0, 1.0])
         out += s * amp * np.exp(-((ys[:, None] - cy) ** 2 + (xs[None, :] - cx) ** 2) / (2 * sigma * sigma))
     return out.astype(np.float32)
+
+
+# Oblique view of the polar scene whose visible surface points are the polar
+# config's shadow-ray origins: camera 10 km above the surface, 30 km from the
+# pole toward grid -y, aimed at the pole, 40 deg vertical field of view,
+# 3840 x 2160 pixels (smaller pixel grids keep the same frustum).
+POLAR_CAMERA = dict(altitude=10e3, offset=30e3, fov_y_deg=40.0, width=3840, height=2160,
+                    step_m=2.5, max_dist_m=150e3)
+
+
+def camera(width=None, height=None, radius=MOON_RADIUS_M):
+    """The polar view as plain numbers: centre ``pos`` (m, tile frame: z through
+    the pole, grid +y = y), orthonormal ``forward``/``right``/``up`` (up in the
+    plane of forward and the local vertical), ``tan_x``/``tan_y`` (half-angle
+    tangents), ``width``/``height`` (pixel (i, j), row 0 at the top, looks along
+    forward + a right + b up with a = (2(i+0.5)/W - 1) tan_x,
+    b = (1 - 2(j+0.5)/H) tan_y), and the march parameters ``step_m``,
+    ``max_dist_m``."""
+    c = POLAR_CAMERA
+    W = c["width"] if width is None else int(width)
+    H = c["height"] if height is None else int(height)
+    th = c["offset"] / radius
+    vert = np.array([0.0, -math.sin(th), math.cos(th)])
+    pos = (radius + c["altitude"]) * vert
+    target = np.array([0.0, 0.0, radius])
+    fwd = target - pos
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, vert)
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    tan_y = math.tan(math.radians(c["fov_y_deg"]) / 2.0)
+    tan_x = tan_y * W / H
+    return dict(pos=pos, forward=fwd, right=right, up=up, tan_x=tan_x, tan_y=tan_y,
+                width=W, height=H, step_m=c["step_m"], max_dist_m=c["max_dist_m"])
