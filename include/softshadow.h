@@ -269,6 +269,42 @@ size_t ss_batch_static_scratch_bytes(void);
 ss_status ss_batch_submit_static(const ss_batch_item* items, int32_t n_items,
                                  const ss_params* params, ss_stream_t stream);
 
+/* ------------------------------------------------------------ view rays --
+ * The terrain points a camera sees: the origins of the shadow rays of a view
+ * (Sec. 4: view rays are intersected with the displaced terrain; the maximum
+ * mipmap lets a ray skip the sample blocks it passes above).
+ *
+ * Pixel (i, j), row 0 at the top, W = width, H = height, looks along
+ *   d = unit(forward + a right + b up), a = (2(i + 0.5)/W - 1) tan_half_x,
+ *   b = (1 - 2(j + 0.5)/H) tan_half_y.
+ * Along x(tau) = pos + tau d the samples tau_k = k step_m, k = 1 ..
+ * floor(max_dist_m / step_m), are tested in order; the hit is the first one
+ * whose texel image lies in [0,nx-1] x [0,ny-1] with |x| - R - h(image) <= 0
+ * (h bilinear); when the sample before it is in the tile too the crossing is
+ * refined by 48 bisection halvings of that step.  All in FP64.
+ *
+ * Output: the hits' texel coordinates (u, v) as float32 pairs in pixel order,
+ * uv[2*r], uv[2*r+1] for r < *count (device int64 written by the call), and
+ * optionally pixel[r] = j*W + i.  Pixels without a hit (sky, off the tile)
+ * produce no entry.  The list feeds ss_shadow_forward as SS_RAYS_LIST rays
+ * (lift 0).  Sizes: uv holds 2*W*H floats, pixel W*H ints; workspace
+ * ss_view_workspace_bytes(W, H) bytes (caller-allocated, device).
+ * Errors: W, H < 1 or W*H >= 2^31 -> SS_ERR_BAD_SIZE; non-finite camera
+ * numbers, step_m <= 0, max_dist_m <= 0, more than 2^31 samples, NULL
+ * pointers or a short workspace -> SS_ERR_INVALID_ARG / SS_ERR_BAD_SIZE. */
+typedef struct {
+    double pos[3];                      /* camera centre, tile frame (m)          */
+    double forward[3], right[3], up[3]; /* orthonormal view frame                 */
+    double tan_half_x, tan_half_y;      /* tangents of the half fields of view   */
+    int32_t width, height;              /* pixels                                 */
+} ss_camera;
+
+size_t ss_view_workspace_bytes(int32_t width, int32_t height);
+ss_status ss_view_rays(const ss_heightfield* hf, const float* mip, const ss_camera* cam,
+                       double step_m, double max_dist_m, float* uv, int32_t* pixel,
+                       int64_t* count, void* workspace, size_t workspace_bytes,
+                       ss_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,13 @@ class SSOutputs(ctypes.Structure):
 SSBatchItem._fields_ = [("hf", SSHeightfield), ("mip", c_vp), ("sun", SSSun), ("out", SSOutputs)]
 
 
+class SSCamera(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_double * 3), ("forward", ctypes.c_double * 3),
+                ("right", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("tan_half_x", ctypes.c_double), ("tan_half_y", ctypes.c_double),
+                ("width", c_i32), ("height", c_i32)]
+
+
 P = ctypes.POINTER
 _SIGNATURES = {
     "ss_status_string": (ctypes.c_char_p, [c_i32]),
@@ -76,6 +83,9 @@ _SIGNATURES = {
                                      P(c_vp)]),
     "ss_batch_plan_launch": (c_i32, [c_vp, c_vp]),
     "ss_batch_plan_destroy": (c_i32, [c_vp]),
+    "ss_view_workspace_bytes": (ctypes.c_size_t, [c_i32, c_i32]),
+    "ss_view_rays": (c_i32, [P(SSHeightfield), c_vp, P(SSCamera), ctypes.c_double,
+                             ctypes.c_double, c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),
 }
 
 _lock = threading.Lock()

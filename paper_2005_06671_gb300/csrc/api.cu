@@ -540,3 +540,54 @@ ss_status ss_batch_submit_static(const ss_batch_item* items, int32_t n_items,
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ view rays
+extern "C" {
+
+size_t ss_view_workspace_bytes(int32_t width, int32_t height) {
+    if (width < 1 || height < 1 || (int64_t)width * height >= ((int64_t)1 << 31)) return 0;
+    return ss::view_workspace_bytes(width, height);
+}
+
+ss_status ss_view_rays(const ss_heightfield* hf, const float* mip, const ss_camera* cam,
+                       double step_m, double max_dist_m, float* uv, int32_t* pixel,
+                       int64_t* count, void* workspace, size_t workspace_bytes,
+                       ss_stream_t stream) {
+    ss_status st = check_tile(hf, 2);
+    if (st != SS_OK) return st;
+    if (!cam || !mip || !uv || !count || !workspace) return SS_ERR_INVALID_ARG;
+    if (cam->width < 1 || cam->height < 1 ||
+        (int64_t)cam->width * cam->height >= ((int64_t)1 << 31))
+        return SS_ERR_BAD_SIZE;
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(cam->pos[k]) || !isfinite(cam->forward[k]) || !isfinite(cam->right[k]) ||
+            !isfinite(cam->up[k]))
+            return SS_ERR_INVALID_ARG;
+    if (!isfinite(cam->tan_half_x) || !isfinite(cam->tan_half_y)) return SS_ERR_INVALID_ARG;
+    if (!finite_pos(step_m) || !finite_pos(max_dist_m)) return SS_ERR_INVALID_ARG;
+    const double K = floor(max_dist_m / step_m);
+    if (!(K >= 1.0) || K >= 2147483648.0) return SS_ERR_BAD_SIZE;
+    if (workspace_bytes < ss_view_workspace_bytes(cam->width, cam->height)) return SS_ERR_BAD_SIZE;
+    ss::MipLayout L;
+    if (!ss::mip_layout(hf->nx, hf->ny, &L)) return SS_ERR_BAD_SIZE;
+    const ss_sun unused = { 0.1, 0.0, 1e-3 };   // the view kernels read only the tile geometry
+    const ss::Tile T = make_tile(hf, &unused, 0, 1.0);
+    const ss::Pyramid P = make_pyramid(hf, mip, L);
+    ss::ViewCamera vc{};
+    for (int k = 0; k < 3; ++k) {
+        vc.pos[k] = cam->pos[k];
+        vc.forward[k] = cam->forward[k];
+        vc.right[k] = cam->right[k];
+        vc.up[k] = cam->up[k];
+    }
+    vc.tan_x = cam->tan_half_x;
+    vc.tan_y = cam->tan_half_y;
+    vc.width = cam->width;
+    vc.height = cam->height;
+    cudaError_t e = ss::launch_view_rays(T, P, vc, step_m, (int64_t)K, mip + L.stats_offset, uv,
+                                         pixel, count, workspace, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_view_rays");
+    return SS_OK;
+}
+
+}  // extern "C"

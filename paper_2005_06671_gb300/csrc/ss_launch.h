@@ -53,6 +53,19 @@ cudaError_t launch_dp_forward(const FwdArgs& a, int block, cudaStream_t s);
 cudaError_t launch_uniform_forward(const FwdArgs& a, int block, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs& a, int block, cudaStream_t s);
 
+// camera of the view-ray caster (mirrors ss_camera)
+struct ViewCamera {
+    double pos[3], forward[3], right[3], up[3];
+    double tan_x, tan_y;
+    int32_t width, height;
+};
+
+int64_t view_blocks(int32_t width, int32_t height);
+size_t view_workspace_bytes(int32_t width, int32_t height);
+cudaError_t launch_view_rays(const Tile& T, const Pyramid& P, const ViewCamera& cam, double step,
+                             int64_t K, const float* stats, float* uv, int32_t* pixel,
+                             int64_t* count, void* workspace, cudaStream_t s);
+
 int device_sm_count();
 
 }  // namespace ss

@@ -1,0 +1,343 @@
+// View rays of a camera against the bilinear terrain: the terrain points a
+// camera sees, which are the origins of the shadow rays (Sec. 4: view rays are
+// intersected with the displaced terrain, and the maximum mipmap lets a ray
+// skip what it passes above).
+//
+// Per pixel (FP64 throughout; this is setup, not the per-sample hot path):
+//   d = unit(forward + a right + b up), x(tau) = C + tau d, samples tau_k = k step;
+//   the hit is the first sample whose texel image is in the tile and lies on or
+//   below the terrain (|x| - R - h <= 0); when the sample before it is in the
+//   tile too the crossing is refined by 48 bisection halvings.
+// Sample blocks are walked near-to-far like the shadow descent (aligned blocks
+// of 2^k samples, next block at s0 += 2^k): a block is skipped when the ray's
+// lowest height over it exceeds the maximum-mipmap value over its texel
+// footprint, or when the footprint misses the tile, so the first sample found
+// below the terrain is the first one overall.
+//
+// Then the hits are compacted in pixel order (per-block counts, one scan block,
+// a scatter), so the ray list is deterministic.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ss_launch.h"
+
+namespace ss {
+
+namespace {
+
+constexpr int kViewBlock = 256;
+constexpr int kViewLeaf = 2;          // blocks of <= 4 samples are tested sample by sample
+constexpr double kViewGuard = 1e-3;   // m: FP64 rounding of heights and bounds is ~1e-9 m
+
+struct Cam {
+    double C[3], f[3], r[3], u[3];
+    double tan_x, tan_y;
+    int32_t W, H;
+};
+
+struct ViewArgs {
+    Tile T;
+    Pyramid P;
+    Cam cam;
+    double step;
+    int64_t K;
+    const float* stats;       // (global max, global min) of the heights
+    float2* pix_uv;           // per pixel: hit texel coords, NaN when none
+    int32_t* block_count;     // per block of kViewBlock pixels
+    int64_t* block_off;       // exclusive prefix of block_count
+    int32_t n_blocks;
+    float* uv_out;
+    int32_t* pixel_out;
+    int64_t* count_out;
+};
+
+// texel image of the direction of x; false without an image (gnomonic: behind
+// the plane; stereographic: the antipode)
+__device__ __forceinline__ bool image(const Tile& T, const double x[3], double& u, double& v) {
+    double X, Y;
+    if (T.proj == 0) {
+        if (!(x[2] > 0.0)) return false;
+        const double k = T.R / x[2];
+        X = x[0] * k;
+        Y = x[1] * k;
+    } else {
+        const double m = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        const double den = m + x[2];
+        if (!(den > 0.0)) return false;
+        const double k = 2.0 * T.R / den;
+        X = x[0] * k;
+        Y = x[1] * k;
+    }
+    u = X / T.g + T.cx;
+    v = Y / T.g + T.cy;
+    return true;
+}
+
+__device__ __forceinline__ bool in_tile(const Tile& T, double u, double v) {
+    return u >= 0.0 && u <= (double)(T.nx - 1) && v >= 0.0 && v <= (double)(T.ny - 1);
+}
+
+// sample at distance tau: in-tile flag, and whether it is on or below the terrain
+__device__ __forceinline__ bool below(const Tile& T, const double C[3], const double d[3],
+                                      double tau, bool& inside, double& u, double& v) {
+    const double x[3] = { C[0] + tau * d[0], C[1] + tau * d[1], C[2] + tau * d[2] };
+    inside = image(T, x, u, v) && in_tile(T, u, v);
+    if (!inside) return false;
+    int32_t i0, j0;
+    double w[4];
+    const double hb = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, u, v, &i0, &j0, w);
+    const double H = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) - T.R;
+    return H - hb <= 0.0;
+}
+
+// maximum of the heights over texel box [x0, x1] x [y0, y1] (inclusive, clamped
+// to the tile), read as <= 2x2 cells of the coarsest level whose cells cover it
+__device__ __forceinline__ float box_max(const Tile& T, const Pyramid& P, int32_t x0, int32_t x1,
+                                         int32_t y0, int32_t y1) {
+    const int32_t ext = max(x1 - x0, y1 - y0);
+    int32_t m = ext <= 1 ? 0 : 31 - __clz(ext);
+    m += (((x1 >> m) - (x0 >> m)) > 1 || ((y1 >> m) - (y0 >> m)) > 1) ? 1 : 0;
+    m = min(m, P.levels - 1);
+    const float* base = P.ptr[m];
+    const int64_t pm = P.pitch[m];
+    const int32_t cx0 = x0 >> m, cx1 = x1 >> m, cy0 = y0 >> m, cy1 = y1 >> m;
+    const float a = base[(int64_t)cy0 * pm + cx0], b = base[(int64_t)cy0 * pm + cx1];
+    const float c = base[(int64_t)cy1 * pm + cx0], e = base[(int64_t)cy1 * pm + cx1];
+    return fmaxf(fmaxf(a, b), fmaxf(c, e));
+}
+
+__global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) {
+    const int64_t npix = (int64_t)a.cam.W * a.cam.H;
+    const int64_t pix = (int64_t)blockIdx.x * kViewBlock + threadIdx.x;
+    bool hit = false;
+    double hu = 0.0, hv = 0.0;
+    if (pix < npix) {
+        const Tile& T = a.T;
+        const Cam& cm = a.cam;
+        const int64_t i = pix % cm.W, j = pix / cm.W;
+        const double aa = (2.0 * ((double)i + 0.5) / (double)cm.W - 1.0) * cm.tan_x;
+        const double bb = (1.0 - 2.0 * ((double)j + 0.5) / (double)cm.H) * cm.tan_y;
+        double d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = cm.f[k] + aa * cm.r[k] + bb * cm.u[k];
+        const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] /= dn;
+        const double* C = cm.C;
+        // samples that can reach the highest height: tau in [tau_in, tau_out]
+        const double hmax = (double)a.stats[0];
+        const double Rm = T.R + hmax;
+        const double cd = C[0] * d[0] + C[1] * d[1] + C[2] * d[2];
+        const double cc = C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
+        const double disc = cd * cd - (cc - Rm * Rm);
+        int64_t k0 = 1, k1 = 0;
+        if (disc >= 0.0) {
+            const double sq = sqrt(disc);
+            const double tau_in = -cd - sq, tau_out = -cd + sq;
+            if (tau_out >= 0.0) {
+                k0 = tau_in > 0.0 ? (int64_t)floor(tau_in / a.step) - 1 : 1;
+                k0 = k0 < 1 ? 1 : k0;
+                k1 = (int64_t)ceil(tau_out / a.step) + 1;
+                k1 = k1 > a.K ? a.K : k1;
+            }
+        }
+        // image circle of the ray (stereographic): 1/(8 r) in texels^-1
+        double inv8r = 0.0;
+        if (T.proj != 0) {
+            const double N[3] = { C[1] * d[2] - C[2] * d[1], C[2] * d[0] - C[0] * d[2],
+                                  C[0] * d[1] - C[1] * d[0] };
+            const double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+            inv8r = nn > 0.0 ? fabs(N[2]) / nn * T.g / (16.0 * T.R) : 0.0;
+        }
+        const double tv = -cd;   // closest approach to the centre
+        if (k0 <= k1) {
+            const int64_t b0 = k0 - 1, n = k1 - b0;
+            int32_t kk = 0;
+            while (((int64_t)1 << kk) < n) ++kk;
+            int64_t s0 = 0;
+            int32_t k = kk;
+            int64_t hit_k = -1;
+            while (s0 < n) {
+                const int64_t ja = b0 + s0 + 1;
+                const int64_t jb = min(b0 + s0 + ((int64_t)1 << k), k1);
+                bool descend = false;
+                if (k <= kViewLeaf) {
+                    for (int64_t q = ja; q <= jb; ++q) {
+                        bool ins;
+                        double u, v;
+                        if (below(T, C, d, (double)q * a.step, ins, u, v)) {
+                            hit_k = q;
+                            break;
+                        }
+                    }
+                    if (hit_k >= 0) break;
+                } else {
+                    const double ta = (double)ja * a.step, tb = (double)jb * a.step;
+                    const double xa[3] = { C[0] + ta * d[0], C[1] + ta * d[1], C[2] + ta * d[2] };
+                    const double xb[3] = { C[0] + tb * d[0], C[1] + tb * d[1], C[2] + tb * d[2] };
+                    double ua, va, ub, vb;
+                    if (!image(T, xa, ua, va) || !image(T, xb, ub, vb)) {
+                        descend = true;
+                    } else {
+                        const double du = ub - ua, dv = vb - va;
+                        const double e = 1e-6 * (fabs(ua) + fabs(ub) + fabs(va) + fabs(vb) + 1.0) +
+                                         (du * du + dv * dv) * inv8r;
+                        const double lo_u = fmin(ua, ub) - e, hi_u = fmax(ua, ub) + e;
+                        const double lo_v = fmin(va, vb) - e, hi_v = fmax(va, vb) + e;
+                        const bool misses = hi_u < 0.0 || lo_u > (double)(T.nx - 1) ||
+                                            hi_v < 0.0 || lo_v > (double)(T.ny - 1);
+                        if (!misses) {
+                            const int32_t x0 = (int32_t)fmax(floor(lo_u), 0.0);
+                            const int32_t x1 = (int32_t)fmin(floor(hi_u) + 1.0, (double)(T.nx - 1));
+                            const int32_t y0 = (int32_t)fmax(floor(lo_v), 0.0);
+                            const int32_t y1 = (int32_t)fmin(floor(hi_v) + 1.0, (double)(T.ny - 1));
+                            const double M = (double)box_max(T, a.P, x0, x1, y0, y1);
+                            const double tc = fmin(fmax(tv, ta), tb);
+                            const double xc[3] = { C[0] + tc * d[0], C[1] + tc * d[1],
+                                                   C[2] + tc * d[2] };
+                            const double Hmin =
+                                sqrt(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]) - T.R;
+                            descend = !(Hmin - M > kViewGuard);
+                        }
+                    }
+                }
+                if (descend) {
+                    --k;
+                } else {
+                    s0 += (int64_t)1 << k;
+                    k = s0 == 0 ? kk : min(__ffsll(s0) - 1, kk);
+                }
+            }
+            if (hit_k >= 0) {
+                double hi = (double)hit_k * a.step;
+                bool prev_in = false;
+                if (hit_k > 1) {
+                    double u, v;
+                    below(T, C, d, (double)(hit_k - 1) * a.step, prev_in, u, v);
+                }
+                if (prev_in) {
+                    double lo = (double)(hit_k - 1) * a.step;
+                    for (int it = 0; it < 48; ++it) {
+                        const double mid = lo + 0.5 * (hi - lo);
+                        bool ins;
+                        double u, v;
+                        if (below(T, C, d, mid, ins, u, v))
+                            hi = mid;
+                        else
+                            lo = mid;
+                    }
+                }
+                const double xh[3] = { C[0] + hi * d[0], C[1] + hi * d[1], C[2] + hi * d[2] };
+                hit = image(T, xh, hu, hv);
+            }
+        }
+        a.pix_uv[pix] = hit ? make_float2((float)hu, (float)hv) : make_float2(NAN, NAN);
+    }
+    const int cnt = __syncthreads_count(hit);
+    if (threadIdx.x == 0) a.block_count[blockIdx.x] = cnt;
+}
+
+// exclusive prefix of the per-block counts (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) view_scan_kernel(const ViewArgs a) {
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int per = (a.n_blocks + 1023) / 1024;
+    const int lo = min(t * per, a.n_blocks), hi = min(lo + per, a.n_blocks);
+    int64_t s = 0;
+    for (int b = lo; b < hi; ++b) s += a.block_count[b];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scan
+        const int64_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = t > 0 ? part[t - 1] : 0;
+    for (int b = lo; b < hi; ++b) {
+        a.block_off[b] = run;
+        run += a.block_count[b];
+    }
+    if (t == 1023) *a.count_out = part[1023];
+}
+
+// scatter the hits of each block to their place in pixel order
+__global__ void __launch_bounds__(kViewBlock) view_compact_kernel(const ViewArgs a) {
+    __shared__ int32_t warp_base[kViewBlock / 32];
+    const int64_t npix = (int64_t)a.cam.W * a.cam.H;
+    const int64_t pix = (int64_t)blockIdx.x * kViewBlock + threadIdx.x;
+    float2 uv = make_float2(NAN, NAN);
+    if (pix < npix) uv = a.pix_uv[pix];
+    const bool hit = !isnan(uv.x);
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) warp_base[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t s = 0;
+        for (int k = 0; k < kViewBlock / 32; ++k) {
+            const int32_t c = warp_base[k];
+            warp_base[k] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+    if (hit) {
+        const int64_t o = a.block_off[blockIdx.x] + warp_base[w] +
+                          __popc(m & ((1u << lane) - 1u));
+        a.uv_out[2 * o] = uv.x;
+        a.uv_out[2 * o + 1] = uv.y;
+        if (a.pixel_out) a.pixel_out[o] = (int32_t)pix;
+    }
+}
+
+}  // namespace
+
+int64_t view_blocks(int32_t width, int32_t height) {
+    return ((int64_t)width * height + kViewBlock - 1) / kViewBlock;
+}
+
+size_t view_workspace_bytes(int32_t width, int32_t height) {
+    const int64_t npix = (int64_t)width * height, nb = view_blocks(width, height);
+    return (size_t)(npix * 8 + nb * 4 + 256 + nb * 8 + 256);
+}
+
+cudaError_t launch_view_rays(const Tile& T, const Pyramid& P, const ViewCamera& vc, double step,
+                             int64_t K, const float* stats, float* uv, int32_t* pixel,
+                             int64_t* count, void* workspace, cudaStream_t s) {
+    ViewArgs a{};
+    a.T = T;
+    a.P = P;
+    for (int k = 0; k < 3; ++k) {
+        a.cam.C[k] = vc.pos[k];
+        a.cam.f[k] = vc.forward[k];
+        a.cam.r[k] = vc.right[k];
+        a.cam.u[k] = vc.up[k];
+    }
+    a.cam.tan_x = vc.tan_x;
+    a.cam.tan_y = vc.tan_y;
+    a.cam.W = vc.width;
+    a.cam.H = vc.height;
+    a.step = step;
+    a.K = K;
+    a.stats = stats;
+    const int64_t npix = (int64_t)vc.width * vc.height, nb = view_blocks(vc.width, vc.height);
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    a.pix_uv = reinterpret_cast<float2*>(ws);
+    size_t off = (size_t)npix * 8;
+    a.block_count = reinterpret_cast<int32_t*>(ws + off);
+    off += (size_t)nb * 4;
+    off = (off + 255) & ~(size_t)255;
+    a.block_off = reinterpret_cast<int64_t*>(ws + off);
+    a.n_blocks = (int32_t)nb;
+    a.uv_out = uv;
+    a.pixel_out = pixel;
+    a.count_out = count;
+    view_hit_kernel<<<(unsigned)nb, kViewBlock, 0, s>>>(a);
+    view_scan_kernel<<<1, 1024, 0, s>>>(a);
+    view_compact_kernel<<<(unsigned)nb, kViewBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ss

@@ -324,3 +324,41 @@ def ss_batch_submit(hfs, suns, max_len_m, **kw):
     outs = b.submit()
     b.close()
     return outs
+
+
+# ------------------------------------------------------------------ view rays
+def _camera(cam):
+    c = _abi.SSCamera()
+    for k in ("pos", "forward", "right", "up"):
+        v = [float(x) for x in cam[k]]
+        getattr(c, k)[:] = v
+    c.tan_half_x = float(cam["tan_x"])
+    c.tan_half_y = float(cam["tan_y"])
+    c.width = int(cam["width"])
+    c.height = int(cam["height"])
+    return c
+
+
+def ss_view_rays(hf: Heightfield, mip, cam, step_m=None, max_dist_m=None, stream=None):
+    """Terrain points seen by a camera (first hit of each pixel's view ray), in
+    pixel order: returns (uv float32 [n, 2], pixel int32 [n]) CUDA tensors.
+    ``cam``: dict with pos, forward, right, up (3-vectors), tan_x, tan_y, width,
+    height and optionally step_m, max_dist_m (as made by ``workloads.camera``)."""
+    L = _abi.lib()
+    step = float(cam["step_m"] if step_m is None else step_m)
+    dist = float(cam["max_dist_m"] if max_dist_m is None else max_dist_m)
+    W, H = int(cam["width"]), int(cam["height"])
+    dev = hf.h.device
+    uv = torch.empty((W * H, 2), dtype=torch.float32, device=dev)
+    pixel = torch.empty(W * H, dtype=torch.int32, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    wsb = L.ss_view_workspace_bytes(W, H)
+    if wsb == 0:
+        raise ValueError("bad camera size")
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    c = _camera(cam)
+    st = L.ss_view_rays(ctypes.byref(hf.c()), _ptr(mip), ctypes.byref(c), step, dist, _ptr(uv),
+                        _ptr(pixel), _ptr(count), _ptr(ws), wsb, _stream_ptr(stream))
+    _abi.check(st, "ss_view_rays")
+    n = int(count.item())
+    return uv[:n], pixel[:n]

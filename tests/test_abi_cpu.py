@@ -140,3 +140,52 @@ def test_other_entry_points_reject_bad_arguments():
                                   ctypes.byref(prm), ctypes.c_void_p(FAKE), None,
                                   ctypes.c_void_p(FAKE), ctypes.c_void_p(FAKE),
                                   ctypes.c_void_p(FAKE), None) == 1
+
+
+def _cam(w=32, h=18):
+    c = _abi.SSCamera()
+    c.pos[:] = [0.0, -30e3, 1747e3]
+    c.forward[:] = [0.0, 0.95, -0.31]
+    c.right[:] = [1.0, 0.0, 0.0]
+    c.up[:] = [0.0, 0.31, 0.95]
+    c.tan_half_x, c.tan_half_y = 0.6, 0.36
+    c.width, c.height = w, h
+    return c
+
+
+@pytest.mark.parametrize("mutate,expect", [
+    (lambda a: a.update(cam=None), 1),
+    (lambda a: a.update(mip=None), 1),
+    (lambda a: a.update(uv=None), 1),
+    (lambda a: a.update(count=None), 1),
+    (lambda a: a.update(ws=None), 1),
+    (lambda a: a.update(cam=_cam(0, 18)), 2),
+    (lambda a: a.update(cam=_cam(65536, 32768)), 2),
+    (lambda a: a["cam"].pos.__setitem__(1, float("nan")), 1),
+    (lambda a: setattr(a["cam"], "tan_half_y", float("inf")), 1),
+    (lambda a: a.update(step=0.0), 1),
+    (lambda a: a.update(dist=-5.0), 1),
+    (lambda a: a.update(step=1e-6, dist=1e6), 2),     # more than 2^31 samples
+    (lambda a: a.update(wsb=a["wsb"] - 1), 2),
+    (lambda a: setattr(a["hf"], "nx", 1), 2),
+])
+def test_view_rays_reject_bad_arguments(mutate, expect):
+    lib = _abi.lib()
+    hf = SSHeightfield(FAKE, 64, 64, 64, 10.0, 1737.4e3, 1)
+    a = dict(hf=hf, cam=_cam(), mip=FAKE, uv=FAKE, count=FAKE, ws=FAKE, step=2.5,
+             dist=150e3, wsb=lib.ss_view_workspace_bytes(32, 18))
+    assert a["wsb"] > 32 * 18 * 8
+    mutate(a)
+    vp = lambda x: ctypes.c_void_p(x) if x else None   # noqa: E731
+    st = lib.ss_view_rays(ctypes.byref(a["hf"]), vp(a["mip"]),
+                          ctypes.byref(a["cam"]) if a["cam"] is not None else None,
+                          a["step"], a["dist"], vp(a["uv"]), None, vp(a["count"]), vp(a["ws"]),
+                          a["wsb"], None)
+    assert st == expect
+
+
+def test_view_workspace_bytes_rejects_bad_sizes():
+    lib = _abi.lib()
+    assert lib.ss_view_workspace_bytes(0, 5) == 0
+    assert lib.ss_view_workspace_bytes(65536, 32768) == 0
+    assert lib.ss_view_workspace_bytes(3840, 2160) >= 3840 * 2160 * 8
