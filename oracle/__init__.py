@@ -9,7 +9,8 @@ and shares no source with it.
   brute force over every sample of every ray, the analytic gradient at the
   argmin, and the maximum mipmap.
   ``view_oracle.c`` adds the first terrain hit of a camera's view rays (the
-  polar scene's ray origins).
+  polar scene's ray origins); ``greedy_oracle.c`` restates the paper's greedy
+  Algorithm 1 (an approximation, reproduced to measure its error).
 * ``oracle.mini`` -- an independent NumPy restatement for tiny inputs, used to
   cross-check the C code.
 
@@ -18,7 +19,7 @@ Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 differences, and the C-vs-NumPy cross-check); none is "parity unpinned".
 """
 from .cref import (build_oracle, disc_light, shadow, ray_costs, sin_elev, grad,
-                   maxmip, num_threads, library_path, view_hits)
+                   maxmip, num_threads, library_path, view_hits, greedy)
 
 __all__ = ["build_oracle", "disc_light", "shadow", "ray_costs", "sin_elev", "grad",
-           "maxmip", "num_threads", "library_path", "view_hits"]
+           "maxmip", "num_threads", "library_path", "view_hits", "greedy"]

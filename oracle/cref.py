@@ -1,4 +1,5 @@
-"""ctypes binding of the C oracle (``shadow_oracle.c``, ``view_oracle.c``).
+"""ctypes binding of the C oracle (``shadow_oracle.c``, ``view_oracle.c``,
+``greedy_oracle.c``).
 Test infrastructure only.
 
 ``build_oracle()`` compiles the C files with gcc (FP64, IEEE semantics: no
@@ -14,7 +15,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "shadow_oracle.c"), os.path.join(_HERE, "view_oracle.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("shadow_oracle.c", "view_oracle.c", "greedy_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -66,6 +67,9 @@ def _load():
             lib.ov_view_hits.restype = None
             lib.ov_view_hits.argtypes = [p, i32, i32, i64, d, d, i32, p, p, p, p, d, d, i32,
                                          i32, d, d, i64, p, p, p]
+            lib.og_greedy.restype = None
+            lib.og_greedy.argtypes = [p, p, i32, i32, d, d, i32, d, d, d, p, i32, i32, i64, p,
+                                      p, p, p, p]
             lib.or_num_threads.restype = i32
             lib.or_num_threads.argtypes = []
             _lib = lib
@@ -208,3 +212,24 @@ def view_hits(h, g, radius, cam, pixels, proj="polar_stereo"):
                      int(cam["height"]), float(cam["step_m"]), float(cam["max_dist_m"]),
                      px.size, _ptr(px), _ptr(u), _ptr(v))
     return u, v
+
+
+def greedy(h, g, radius, elev, az, alpha, levels=(5, 5, 5), proj="gnomonic", uv=None,
+           lift=None):
+    """The paper's greedy descent (Algorithm 1 with interval concatenation), FP64:
+    returns (light, cost J [rad, +inf if nothing sampled], t* [m, -1]) per ray;
+    ``levels`` = N' of each run."""
+    lib = _load()
+    h32 = np.ascontiguousarray(h, dtype=np.float32)
+    h64 = h32.astype(np.float64)
+    ny, nx = h32.shape
+    mode, n, uvp, liftp = _rays(uv, lift)
+    nr = nx * ny if mode == 0 else n
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    light = np.empty(nr)
+    cost = np.empty(nr)
+    tstar = np.empty(nr)
+    lib.og_greedy(_ptr(h32), _ptr(h64), nx, ny, float(g), float(radius), PROJ[proj],
+                  float(elev), float(az), float(alpha), _ptr(lv), lv.size, mode, n, _ptr(uvp),
+                  _ptr(liftp), _ptr(light), _ptr(cost), _ptr(tstar))
+    return light, cost, tstar
