@@ -325,6 +325,28 @@ def run_ours(args):
                          "note": "SS_FLAG_LIGHT_ONLY: same step, exact light; argmin exact "
                                  "in the penumbra only"}
 
+    # ---- the paper's greedy descent (Algorithm 1, N' = {5,5,5}; an approximation):
+    #      its speed here and its light error against the exact descent
+    g_ms = []
+    for k in range(3):
+        flush.zero_()
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        ss.ss_build_maxmip(hf, mip)
+        e1.record(stream)
+        gres = ss.ss_shadow_greedy(hf, mip, sun, levels=(5, 5, 5))
+        e2.record(stream)
+        torch.cuda.synchronize()
+        g_ms.append(e0.elapsed_time(e2))
+    gerr = (gres["light"] - res["light"]).abs()
+    out["greedy"] = {"value": n_rays / (statistics.mean(g_ms) / 1e3), "unit": UNIT,
+                     "ms_per_step": statistics.mean(g_ms), "levels": [5, 5, 5],
+                     "max_light_err_vs_exact": float(gerr.max()),
+                     "mean_light_err_vs_exact": float(gerr.mean()),
+                     "frac_rays_err_gt_1e-5": float((gerr > 1e-5).float().mean()),
+                     "note": "the paper's Algorithm 1 with interval concatenation (FP64): "
+                             "an approximation, not held to the 1e-5 bar"}
+
     # ---- forward + backward (loss gradient of ones), rays/s
     gl = torch.ones(n_rays, dtype=torch.float32, device=dev)
     cost_buf = torch.empty(n_rays, dtype=torch.float32, device=dev)

@@ -269,6 +269,32 @@ size_t ss_batch_static_scratch_bytes(void);
 ss_status ss_batch_submit_static(const ss_batch_item* items, int32_t n_items,
                                  const ss_params* params, ss_stream_t stream);
 
+/* ------------------------------------------------------ greedy descent --
+ * The paper's own greedy descent (Algorithm 1, ray length T of Eq. maxstep,
+ * interval concatenation of Sec. 3.3 "Long shadows"), an APPROXIMATION of the
+ * minimum that ss_shadow_forward computes exactly; provided to reproduce the
+ * paper's method and measure its error.  Run r covers [a_r, a_r + T_r] with
+ * N'_r = levels[r] mip levels: T_r is the ray parameter closest to the line
+ * from the sphere's centre through the texel point 2^(N'_r - 1) texels from the
+ * run start's texel image along the unit texture-plane direction of (s_x, s_y);
+ * with t in [0, 1] over the run, level k = 0 .. N'_r - 1 reads maximum-mipmap
+ * level N'_r - 1 - k (the texel containing the tip's texel image, no filtering)
+ * at t_k, t_k - 2^-(k+1), t_k - 2^-k (t_0 = 1), keeps the smallest
+ * Delta = tip height over the sphere - M (first on ties; tips at t <= 0 or off
+ * the tile are skipped) and continues from t* + 2^-(k+1); the run's cost is the
+ * last level's Delta* over its distance, the ray's the smallest run cost.
+ * light as for ss_shadow_forward.  All in FP64.
+ * Inputs: hf, mip (ss_build_maxmip), rays (grid or list), sun; levels[n_runs]
+ * (host), 1 <= n_runs <= SS_GREEDY_MAX_RUNS, 1 <= levels[r] <=
+ * ss_maxmip_levels(nx, ny).  Outputs (device, one per ray): light; cost (rad,
+ * +inf when no tip was read) and t_star (m, -1 then) optional (NULL).
+ * Errors: as ss_shadow_forward for hf, rays and sun; bad levels/n_runs ->
+ * SS_ERR_INVALID_ARG. */
+#define SS_GREEDY_MAX_RUNS 8
+ss_status ss_shadow_greedy(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                           const ss_sun* sun, const int32_t* levels, int32_t n_runs,
+                           float* light, float* cost, float* t_star, ss_stream_t stream);
+
 /* ------------------------------------------------------------ view rays --
  * The terrain points a camera sees: the origins of the shadow rays of a view
  * (Sec. 4: view rays are intersected with the displaced terrain; the maximum

@@ -591,3 +591,37 @@ ss_status ss_view_rays(const ss_heightfield* hf, const float* mip, const ss_came
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ greedy descent
+extern "C" {
+
+ss_status ss_shadow_greedy(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                           const ss_sun* sun, const int32_t* levels, int32_t n_runs,
+                           float* light, float* cost, float* t_star, ss_stream_t stream) {
+    ss_status st = check_tile(hf, 2);
+    if (st != SS_OK) return st;
+    if ((st = check_sun(sun)) != SS_OK) return st;
+    int64_t n;
+    if ((st = check_rays(rays, hf, &n)) != SS_OK) return st;
+    if (!mip || !levels || n_runs < 1 || n_runs > SS_GREEDY_MAX_RUNS) return SS_ERR_INVALID_ARG;
+    const int32_t L = ss_maxmip_levels(hf->nx, hf->ny);
+    for (int i = 0; i < n_runs; ++i)
+        if (levels[i] < 1 || levels[i] > L) return SS_ERR_INVALID_ARG;
+    if (n == 0) return SS_OK;
+    if (!light) return SS_ERR_INVALID_ARG;
+    ss::MipLayout ML;
+    if (!ss::mip_layout(hf->nx, hf->ny, &ML)) return SS_ERR_BAD_SIZE;
+    const ss::Tile T = make_tile(hf, sun, 0, hf->texel_m);
+    const ss::Pyramid P = make_pyramid(hf, mip, ML);
+    ss::Rays R{};
+    R.mode = rays->mode;
+    R.n = n;
+    R.uv = rays->uv;
+    R.lift = rays->mode == SS_RAYS_LIST ? rays->lift_m : nullptr;
+    cudaError_t e = ss::launch_greedy(T, P, R, levels, n_runs, light, cost, t_star,
+                                      (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_shadow_greedy");
+    return SS_OK;
+}
+
+}  // extern "C"

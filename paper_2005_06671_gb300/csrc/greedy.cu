@@ -1,0 +1,166 @@
+// The paper's greedy descent (Algorithm 1 with the ray length T of Eq. maxstep
+// and the interval concatenation of Sec. 3.3 "Long shadows"): an approximation
+// of the minimum, reproduced so that its error against the exact descent can be
+// measured on the same GPU.  One thread per ray, FP64 (3 tip samples per level,
+// N' levels per run, a handful of runs: ~45 samples per ray).
+//
+// Per run r (starting at distance a_r along the ray):
+//   T_r: the ray parameter closest to the line through the sphere's centre and
+//        the texel point 2^(N'-1) texels from the run start's texel image along
+//        the sun's texture-plane direction (s_x, s_y);
+//   t_0 = 1; level k = 0 .. N'-1 reads mip level m = N'-1-k at the tips
+//        t_k, t_k - 2^-(k+1), t_k - 2^-k (distance a_r + t T_r), keeping the
+//        smallest Delta = H - M (H = tip height over the sphere, M = the level-m
+//        texel containing the tip's texel image; the first one on ties); tips at
+//        t <= 0 or off the tile are not read; then t_{k+1} = t* + 2^-(k+1), or
+//        t_k - 2^-k when no tip was read;
+//   J_r = Delta* / (a_r + t* T_r) of the last level.
+// The ray's cost is the smallest J_r; light = F(clamp(J cos(eps_p)/alpha, -1, 1)).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ss_launch.h"
+#include "ss_walk.cuh"
+
+namespace ss {
+
+namespace {
+
+struct GreedyArgs {
+    Tile T;
+    Pyramid P;
+    Rays R;
+    float* light;
+    float* cost;
+    float* t_star;
+    int32_t n_runs;
+    int32_t levels[kGreedyMaxRuns];
+};
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Eq. maxstep for a run starting at point Rs: length of the run
+__device__ double run_length(const Tile& T, const double Rs[3], const double s[3], int32_t m0) {
+    double u0, v0;
+    if (!texel_image64(T, Rs, u0, v0)) return -1.0;
+    const double ln = sqrt(s[0] * s[0] + s[1] * s[1]);
+    if (!(ln > 0.0)) return -1.0;
+    const double span = ldexp(1.0, m0);
+    double e[3];
+    texel_dir64(T, u0 + span * s[0] / ln, v0 + span * s[1] / ln, e);
+    const double c[3] = { -Rs[0], -Rs[1], -Rs[2] };
+    double ce[3], se[3];
+    cross3(c, e, ce);
+    cross3(s, e, se);
+    const double den = dot3(se, se);
+    if (!(den > 0.0)) return -1.0;
+    return dot3(ce, se) / den;
+}
+
+// one tip: true and delta = H - M when its texel image lies in the tile
+__device__ __forceinline__ bool tip(const Tile& T, const Pyramid& P, const double p[3],
+                                    const double s[3], double dist, int32_t m, double& delta) {
+    const double q[3] = { p[0] + dist * s[0], p[1] + dist * s[1], p[2] + dist * s[2] };
+    double u, v;
+    if (!texel_image64(T, q, u, v) || !in_tile64(T, u, v)) return false;
+    const double cell = ldexp(1.0, m);
+    const int32_t w = ((T.nx - 1) >> m) + 1, h = ((T.ny - 1) >> m) + 1;
+    const int32_t I = min(max((int32_t)floor((u + 0.5) / cell), 0), w - 1);
+    const int32_t J = min(max((int32_t)floor((v + 0.5) / cell), 0), h - 1);
+    const double M = (double)P.ptr[m][(int64_t)J * P.pitch[m] + I];
+    delta = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - T.R - M;
+    return true;
+}
+
+__global__ void __launch_bounds__(256) greedy_kernel(const GreedyArgs a) {
+    const Tile& T = a.T;
+    const int64_t n = ray_count(T, a.R);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double s[3] = { T.sx, T.sy, T.sz };
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        double up, vp, hp, href, ow[4];
+        int32_t oi0, oj0;
+        ray_origin(T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
+        double nv[3];
+        texel_dir64(T, up, vp, nv);
+        const double rho = T.R + hp;
+        const double p[3] = { rho * nv[0], rho * nv[1], rho * nv[2] };
+        double bestJ = INFINITY, bestd = -1.0, start = 0.0;
+        for (int32_t run = 0; run < a.n_runs; ++run) {
+            const int32_t Np = a.levels[run];
+            const double Rs[3] = { p[0] + start * s[0], p[1] + start * s[1], p[2] + start * s[2] };
+            const double Tr = run_length(T, Rs, s, Np - 1);
+            if (!(Tr > 0.0)) break;
+            double tk = 1.0, dstar = INFINITY, ts = -1.0;
+            for (int32_t k = 0; k < Np; ++k) {
+                const int32_t m = min(Np - 1 - k, a.P.levels - 1);
+                const double step = ldexp(1.0, -(k + 1));
+                dstar = INFINITY;
+                ts = -1.0;
+                for (int i = 0; i < 3; ++i) {
+                    if (i > 0) tk -= step;
+                    double dl;
+                    if (tk > 0.0 && tip(T, a.P, p, s, start + tk * Tr, m, dl) && dl < dstar) {
+                        dstar = dl;
+                        ts = tk;
+                    }
+                }
+                if (ts > -1.0) tk = ts + step;
+            }
+            if (ts > -1.0) {
+                const double dist = start + ts * Tr;
+                const double J = dstar / dist;
+                if (J < bestJ) {
+                    bestJ = J;
+                    bestd = dist;
+                }
+            }
+            start += Tr;
+        }
+        float light = 1.0f;
+        if (bestd > 0.0) {
+            const double se = dot3(nv, s);
+            const double ce = sqrt(fmax(0.0, 1.0 - se * se));
+            light = (float)disc_light64(bestJ * ce / T.alpha);
+        }
+        a.light[r] = light;
+        if (a.cost) a.cost[r] = (float)bestJ;
+        if (a.t_star) a.t_star[r] = (float)bestd;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_greedy(const Tile& T, const Pyramid& P, const Rays& R, const int32_t* levels,
+                          int32_t n_runs, float* light, float* cost, float* t_star,
+                          cudaStream_t s) {
+    GreedyArgs a{};
+    a.T = T;
+    a.P = P;
+    a.R = R;
+    a.light = light;
+    a.cost = cost;
+    a.t_star = t_star;
+    a.n_runs = n_runs;
+    for (int i = 0; i < n_runs && i < kGreedyMaxRuns; ++i) a.levels[i] = levels[i];
+    const int64_t n = R.mode == 0 ? (int64_t)T.nx * T.ny : R.n;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, greedy_kernel, 256, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t cap = (int64_t)device_sm_count() * per_sm, want = (n + 255) / 256;
+    const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    greedy_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ss

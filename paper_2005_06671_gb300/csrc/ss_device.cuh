@@ -692,6 +692,50 @@ __device__ __forceinline__ double leaf_cost64(const Tile& T, const Geom64& G, in
     return ((G.hp - hb) + rise64(G, t)) / t;
 }
 
+// ------------------------------------------------ FP64 mapping helpers
+// unit direction of texel coordinates (u, v) under the tile's mapping
+__device__ __forceinline__ void texel_dir64(const Tile& T, double u, double v, double n[3]) {
+    const double X = (u - T.cx) * T.g, Y = (v - T.cy) * T.g;
+    if (T.proj == 0) {
+        const double im = rsqrt(X * X + Y * Y + T.R * T.R);
+        n[0] = X * im;
+        n[1] = Y * im;
+        n[2] = T.R * im;
+    } else {
+        const double fr = 4.0 * T.R * T.R, r2 = X * X + Y * Y, id = 1.0 / (fr + r2);
+        n[0] = 4.0 * T.R * X * id;
+        n[1] = 4.0 * T.R * Y * id;
+        n[2] = (fr - r2) * id;
+    }
+}
+
+// texel image of the direction of point x; false without an image (gnomonic:
+// not in front of the plane; stereographic: the antipode)
+__device__ __forceinline__ bool texel_image64(const Tile& T, const double x[3], double& u,
+                                              double& v) {
+    double X, Y;
+    if (T.proj == 0) {
+        if (!(x[2] > 0.0)) return false;
+        const double k = T.R / x[2];
+        X = x[0] * k;
+        Y = x[1] * k;
+    } else {
+        const double m = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        const double den = m + x[2];
+        if (!(den > 0.0)) return false;
+        const double k = 2.0 * T.R / den;
+        X = x[0] * k;
+        Y = x[1] * k;
+    }
+    u = X / T.g + T.cx;
+    v = Y / T.g + T.cy;
+    return true;
+}
+
+__device__ __forceinline__ bool in_tile64(const Tile& T, double u, double v) {
+    return u >= 0.0 && u <= (double)(T.nx - 1) && v >= 0.0 && v <= (double)(T.ny - 1);
+}
+
 __device__ __forceinline__ double disc_light64(double d) {
     if (d <= -1.0) return 0.0;
     if (d >= 1.0) return 1.0;

@@ -66,6 +66,11 @@ cudaError_t launch_view_rays(const Tile& T, const Pyramid& P, const ViewCamera& 
                              int64_t K, const float* stats, float* uv, int32_t* pixel,
                              int64_t* count, void* workspace, cudaStream_t s);
 
+constexpr int kGreedyMaxRuns = 8;
+cudaError_t launch_greedy(const Tile& T, const Pyramid& P, const Rays& R, const int32_t* levels,
+                          int32_t n_runs, float* light, float* cost, float* t_star,
+                          cudaStream_t s);
+
 int device_sm_count();
 
 }  // namespace ss

@@ -52,37 +52,11 @@ struct ViewArgs {
     int64_t* count_out;
 };
 
-// texel image of the direction of x; false without an image (gnomonic: behind
-// the plane; stereographic: the antipode)
-__device__ __forceinline__ bool image(const Tile& T, const double x[3], double& u, double& v) {
-    double X, Y;
-    if (T.proj == 0) {
-        if (!(x[2] > 0.0)) return false;
-        const double k = T.R / x[2];
-        X = x[0] * k;
-        Y = x[1] * k;
-    } else {
-        const double m = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-        const double den = m + x[2];
-        if (!(den > 0.0)) return false;
-        const double k = 2.0 * T.R / den;
-        X = x[0] * k;
-        Y = x[1] * k;
-    }
-    u = X / T.g + T.cx;
-    v = Y / T.g + T.cy;
-    return true;
-}
-
-__device__ __forceinline__ bool in_tile(const Tile& T, double u, double v) {
-    return u >= 0.0 && u <= (double)(T.nx - 1) && v >= 0.0 && v <= (double)(T.ny - 1);
-}
-
 // sample at distance tau: in-tile flag, and whether it is on or below the terrain
 __device__ __forceinline__ bool below(const Tile& T, const double C[3], const double d[3],
                                       double tau, bool& inside, double& u, double& v) {
     const double x[3] = { C[0] + tau * d[0], C[1] + tau * d[1], C[2] + tau * d[2] };
-    inside = image(T, x, u, v) && in_tile(T, u, v);
+    inside = texel_image64(T, x, u, v) && in_tile64(T, u, v);
     if (!inside) return false;
     int32_t i0, j0;
     double w[4];
@@ -177,7 +151,7 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
                     const double xa[3] = { C[0] + ta * d[0], C[1] + ta * d[1], C[2] + ta * d[2] };
                     const double xb[3] = { C[0] + tb * d[0], C[1] + tb * d[1], C[2] + tb * d[2] };
                     double ua, va, ub, vb;
-                    if (!image(T, xa, ua, va) || !image(T, xb, ub, vb)) {
+                    if (!texel_image64(T, xa, ua, va) || !texel_image64(T, xb, ub, vb)) {
                         descend = true;
                     } else {
                         const double du = ub - ua, dv = vb - va;
@@ -229,7 +203,7 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
                     }
                 }
                 const double xh[3] = { C[0] + hi * d[0], C[1] + hi * d[1], C[2] + hi * d[2] };
-                hit = image(T, xh, hu, hv);
+                hit = texel_image64(T, xh, hu, hv);
             }
         }
         a.pix_uv[pix] = hit ? make_float2((float)hu, (float)hv) : make_float2(NAN, NAN);

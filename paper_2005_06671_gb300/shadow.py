@@ -362,3 +362,22 @@ def ss_view_rays(hf: Heightfield, mip, cam, step_m=None, max_dist_m=None, stream
     _abi.check(st, "ss_view_rays")
     n = int(count.item())
     return uv[:n], pixel[:n]
+
+
+# ------------------------------------------------------------ greedy descent
+def ss_shadow_greedy(hf: Heightfield, mip, sun: Sun, levels=(5, 5, 5), uv=None, lift=None,
+                     stream=None):
+    """The paper's greedy descent (an approximation of ss_shadow_forward's exact
+    minimum): dict(light, cost [rad], t_star [m]) per ray; ``levels`` = N' per run."""
+    L = _abi.lib()
+    rays, n = _rays(hf, uv, lift)
+    dev = hf.h.device
+    light = torch.empty(n, dtype=torch.float32, device=dev)
+    cost = torch.empty(n, dtype=torch.float32, device=dev)
+    t_star = torch.empty(n, dtype=torch.float32, device=dev)
+    lv = (ctypes.c_int32 * len(levels))(*[int(x) for x in levels])
+    st = L.ss_shadow_greedy(ctypes.byref(hf.c()), _ptr(mip), ctypes.byref(rays),
+                            ctypes.byref(sun.c()), ctypes.cast(lv, ctypes.c_void_p), len(levels),
+                            _ptr(light), _ptr(cost), _ptr(t_star), _stream_ptr(stream))
+    _abi.check(st, "ss_shadow_greedy")
+    return {"light": light, "cost": cost, "t_star": t_star}

@@ -189,3 +189,16 @@ def test_view_workspace_bytes_rejects_bad_sizes():
     assert lib.ss_view_workspace_bytes(0, 5) == 0
     assert lib.ss_view_workspace_bytes(65536, 32768) == 0
     assert lib.ss_view_workspace_bytes(3840, 2160) >= 3840 * 2160 * 8
+
+
+@pytest.mark.parametrize("levels,expect", [((5, 5, 5), None), ((), 1), ((0,), 1), ((8,), 1),
+                                           ((5,) * 9, 1), ((7, 3), None)])
+def test_greedy_rejects_bad_levels(levels, expect):
+    lib = _abi.lib()
+    hf, sun, prm, rays, out = _good()          # 64 x 64: 7 mip levels
+    lv = (ctypes.c_int32 * max(len(levels), 1))(*levels)
+    st = lib.ss_shadow_greedy(ctypes.byref(hf), ctypes.c_void_p(FAKE), ctypes.byref(rays),
+                              ctypes.byref(sun), ctypes.cast(lv, ctypes.c_void_p), len(levels),
+                              None, None, None, None)
+    # valid levels pass validation and then need an output pointer
+    assert st == (1 if expect is None else expect)
