@@ -10,7 +10,8 @@ and shares no source with it.
   argmin, and the maximum mipmap.
   ``view_oracle.c`` adds the first terrain hit of a camera's view rays (the
   polar scene's ray origins); ``greedy_oracle.c`` restates the paper's greedy
-  Algorithm 1 (an approximation, reproduced to measure its error).
+  Algorithm 1 (an approximation, reproduced to measure its error);
+  ``shade_oracle.c`` the Lambertian shading of the lit fractions.
 * ``oracle.mini`` -- an independent NumPy restatement for tiny inputs, used to
   cross-check the C code.
 
@@ -19,7 +20,8 @@ Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 differences, and the C-vs-NumPy cross-check); none is "parity unpinned".
 """
 from .cref import (build_oracle, disc_light, shadow, ray_costs, sin_elev, grad,
-                   maxmip, num_threads, library_path, view_hits, greedy)
+                   maxmip, num_threads, library_path, view_hits, greedy,
+                   shade)
 
 __all__ = ["build_oracle", "disc_light", "shadow", "ray_costs", "sin_elev", "grad",
-           "maxmip", "num_threads", "library_path", "view_hits", "greedy"]
+           "maxmip", "num_threads", "library_path", "view_hits", "greedy", "shade"]

@@ -1,5 +1,5 @@
 """ctypes binding of the C oracle (``shadow_oracle.c``, ``view_oracle.c``,
-``greedy_oracle.c``).
+``greedy_oracle.c``, ``shade_oracle.c``).
 Test infrastructure only.
 
 ``build_oracle()`` compiles the C files with gcc (FP64, IEEE semantics: no
@@ -15,7 +15,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, f) for f in ("shadow_oracle.c", "view_oracle.c", "greedy_oracle.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("shadow_oracle.c", "view_oracle.c", "greedy_oracle.c",
+                                          "shade_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -70,6 +71,8 @@ def _load():
             lib.og_greedy.restype = None
             lib.og_greedy.argtypes = [p, p, i32, i32, d, d, i32, d, d, d, p, i32, i32, i64, p,
                                       p, p, p, p]
+            lib.os_shade.restype = None
+            lib.os_shade.argtypes = [p, i32, i32, d, d, i32, i32, i64, p, i32, p, p, p, p, p]
             lib.or_num_threads.restype = i32
             lib.or_num_threads.argtypes = []
             _lib = lib
@@ -233,3 +236,25 @@ def greedy(h, g, radius, elev, az, alpha, levels=(5, 5, 5), proj="gnomonic", uv=
                   float(elev), float(az), float(alpha), _ptr(lv), lv.size, mode, n, _ptr(uvp),
                   _ptr(liftp), _ptr(light), _ptr(cost), _ptr(tstar))
     return light, cost, tstar
+
+
+def shade(h, g, radius, lights, proj="gnomonic", uv=None):
+    """Lambertian irradiance sum_l I_l s_l max(0, N . L_l) per ray (FP64).
+    ``lights``: list of (elevation, azimuth, intensity, lit fraction array [n])."""
+    lib = _load()
+    h64 = _heights(h)
+    ny, nx = h64.shape
+    mode, n, uvp, _ = _rays(uv, None)
+    nr = nx * ny if mode == 0 else n
+    el = np.array([float(x[0]) for x in lights])
+    az = np.array([float(x[1]) for x in lights])
+    it = np.array([float(x[2]) for x in lights])
+    fr = [np.ascontiguousarray(x[3], dtype=np.float64).reshape(-1) for x in lights]
+    for f in fr:
+        assert f.size == nr
+    ptrs = (ctypes.c_void_p * len(fr))(*[f.ctypes.data for f in fr])
+    E = np.empty(nr)
+    lib.os_shade(_ptr(h64), nx, ny, float(g), float(radius), PROJ[proj], mode, n, _ptr(uvp),
+                 len(lights), _ptr(el), _ptr(az), _ptr(it), ctypes.cast(ptrs, ctypes.c_void_p),
+                 _ptr(E))
+    return E
