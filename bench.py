@@ -347,6 +347,46 @@ def run_ours(args):
                      "note": "the paper's Algorithm 1 with interval concatenation (FP64): "
                              "an approximation, not held to the 1e-5 bar"}
 
+    # ---- shading epilogue: Sun and Earth lit fractions -> Lambertian irradiance
+    from workloads import EARTH_LIGHT
+    earth = ss.Sun(math.radians(EARTH_LIGHT["elevation_deg"]),
+                   math.radians(EARTH_LIGHT["azimuth_deg"]),
+                   math.radians(EARTH_LIGHT["angular_radius_deg"]))
+    lit_s = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    lit_e = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    arg_e = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    irr = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    elev, az = inst["suns"][0]
+    lights = [(elev, az, 1.0, lit_s),
+              (earth.elevation, earth.azimuth, EARTH_LIGHT["intensity"], lit_e)]
+    sh_ms, fr_ms = [], []
+    for k in range(3):
+        flush.zero_()
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        ss.ss_build_maxmip(hf, mip)
+        ss.ss_shadow_forward(hf, mip, sun, lmax, out=dict(light=lit_s, argmin=argmin),
+                             want_cost=False)
+        ss.ss_shadow_forward(hf, mip, earth, lmax, out=dict(light=lit_e, argmin=arg_e),
+                             want_cost=False)
+        ss.ss_shade(hf, lights, out=irr)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fr_ms.append(e0.elapsed_time(e2))
+        flush.zero_()
+        e0.record(stream)
+        ss.ss_shade(hf, lights, out=irr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sh_ms.append(e0.elapsed_time(e1))
+    shade_bytes = n_rays * (4.0 * len(lights) + 4.0 + 4.0)
+    out["shade"] = {"value": n_rays / (statistics.mean(fr_ms) / 1e3), "unit": UNIT,
+                    "ms_per_frame": statistics.mean(fr_ms),
+                    "frame": "maxmip + descent for the Sun + descent for the Earth + shading",
+                    "shade_kernel_ms": statistics.mean(sh_ms),
+                    "shade_kernel_gbs": shade_bytes / (statistics.mean(sh_ms) / 1e3) / 1e9,
+                    "shade_algorithmic_bytes": shade_bytes, "peak_gbs": peak}
+
     # ---- forward + backward (loss gradient of ones), rays/s
     gl = torch.ones(n_rays, dtype=torch.float32, device=dev)
     cost_buf = torch.empty(n_rays, dtype=torch.float32, device=dev)

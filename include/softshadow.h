@@ -295,6 +295,30 @@ ss_status ss_shadow_greedy(const ss_heightfield* hf, const float* mip, const ss_
                            const ss_sun* sun, const int32_t* levels, int32_t n_runs,
                            float* light, float* cost, float* t_star, ss_stream_t stream);
 
+/* ----------------------------------------------------- shading epilogue --
+ * Lambertian irradiance of the terrain under several disc lights (Sec. 3.4:
+ * the Sun and the Earth are discs and each has its own lit fraction s_l, from
+ * ss_shadow_forward with that light as the "sun"; Sec. 6.3: Lambertian BRDF):
+ *   E = sum_l intensity_l * s_l * max(0, N . L_l)
+ * L_l from elevation/azimuth as for ss_sun; N the unit normal of the terrain
+ * surface r(u, v) = (R + h(u, v)) n(u, v) at the ray origin: grid rays take
+ * h_u, h_v as central differences of the texel values (one-sided on the
+ * border), listed rays the gradient of the bilinear interpolant in their cell
+ * (lift is ignored: the normal is the terrain's).  float32.
+ * Inputs: hf, rays (as for ss_shadow_forward); lights[n_lights] (host array,
+ * 1 <= n_lights <= SS_SHADE_MAX_LIGHTS) whose `lit` arrays are device float
+ * [n rays].  Output: irradiance (device float [n rays]).
+ * Errors: as ss_shadow_forward for hf and rays; bad lights -> SS_ERR_INVALID_ARG. */
+#define SS_SHADE_MAX_LIGHTS 8
+typedef struct {
+    double elevation_rad, azimuth_rad;   /* light direction (tile-centre frame)     */
+    double intensity;                    /* irradiance at normal incidence, unlit 0 */
+    const float* lit;                    /* device: lit fraction per ray            */
+} ss_light;
+
+ss_status ss_shade(const ss_heightfield* hf, const ss_rays* rays, const ss_light* lights,
+                   int32_t n_lights, float* irradiance, ss_stream_t stream);
+
 /* ------------------------------------------------------------ view rays --
  * The terrain points a camera sees: the origins of the shadow rays of a view
  * (Sec. 4: view rays are intersected with the displaced terrain; the maximum

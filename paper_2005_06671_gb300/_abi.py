@@ -55,6 +55,11 @@ class SSOutputs(ctypes.Structure):
 SSBatchItem._fields_ = [("hf", SSHeightfield), ("mip", c_vp), ("sun", SSSun), ("out", SSOutputs)]
 
 
+class SSLight(ctypes.Structure):
+    _fields_ = [("elevation_rad", ctypes.c_double), ("azimuth_rad", ctypes.c_double),
+                ("intensity", ctypes.c_double), ("lit", c_vp)]
+
+
 class SSCamera(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_double * 3), ("forward", ctypes.c_double * 3),
                 ("right", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
@@ -85,6 +90,7 @@ _SIGNATURES = {
     "ss_batch_plan_destroy": (c_i32, [c_vp]),
     "ss_shadow_greedy": (c_i32, [P(SSHeightfield), c_vp, P(SSRays), P(SSSun), c_vp, c_i32,
                                  c_vp, c_vp, c_vp, c_vp]),
+    "ss_shade": (c_i32, [P(SSHeightfield), P(SSRays), c_vp, c_i32, c_vp, c_vp]),
     "ss_view_workspace_bytes": (ctypes.c_size_t, [c_i32, c_i32]),
     "ss_view_rays": (c_i32, [P(SSHeightfield), c_vp, P(SSCamera), ctypes.c_double,
                              ctypes.c_double, c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),

@@ -625,3 +625,39 @@ ss_status ss_shadow_greedy(const ss_heightfield* hf, const float* mip, const ss_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------- shading epilogue
+extern "C" {
+
+ss_status ss_shade(const ss_heightfield* hf, const ss_rays* rays, const ss_light* lights,
+                   int32_t n_lights, float* irradiance, ss_stream_t stream) {
+    ss_status st = check_tile(hf, 2);
+    if (st != SS_OK) return st;
+    int64_t n;
+    if ((st = check_rays(rays, hf, &n)) != SS_OK) return st;
+    if (!lights || n_lights < 1 || n_lights > SS_SHADE_MAX_LIGHTS) return SS_ERR_INVALID_ARG;
+    ss::ShadeLight L[ss::kShadeMaxLights];
+    for (int l = 0; l < n_lights; ++l) {
+        const ss_light& x = lights[l];
+        if (!isfinite(x.elevation_rad) || !isfinite(x.azimuth_rad) || !isfinite(x.intensity) ||
+            !(fabs(x.elevation_rad) <= M_PI / 2) || !x.lit)
+            return SS_ERR_INVALID_ARG;
+        L[l].elevation_rad = x.elevation_rad;
+        L[l].azimuth_rad = x.azimuth_rad;
+        L[l].intensity = x.intensity;
+        L[l].lit = x.lit;
+    }
+    if (n == 0) return SS_OK;
+    if (!irradiance) return SS_ERR_INVALID_ARG;
+    const ss_sun unused = { 0.1, 0.0, 1e-3 };   // only the tile geometry is read
+    const ss::Tile T = make_tile(hf, &unused, 0, 1.0);
+    ss::Rays R{};
+    R.mode = rays->mode;
+    R.n = n;
+    R.uv = rays->uv;
+    cudaError_t e = ss::launch_shade(T, R, L, n_lights, irradiance, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_shade");
+    return SS_OK;
+}
+
+}  // extern "C"

@@ -71,6 +71,14 @@ cudaError_t launch_greedy(const Tile& T, const Pyramid& P, const Rays& R, const 
                           int32_t n_runs, float* light, float* cost, float* t_star,
                           cudaStream_t s);
 
+constexpr int kShadeMaxLights = 8;
+struct ShadeLight {       // mirrors ss_light
+    double elevation_rad, azimuth_rad, intensity;
+    const float* lit;
+};
+cudaError_t launch_shade(const Tile& T, const Rays& R, const ShadeLight* lights, int32_t n_lights,
+                         float* E, cudaStream_t s);
+
 int device_sm_count();
 
 }  // namespace ss

@@ -381,3 +381,25 @@ def ss_shadow_greedy(hf: Heightfield, mip, sun: Sun, levels=(5, 5, 5), uv=None, 
                             _ptr(light), _ptr(cost), _ptr(t_star), _stream_ptr(stream))
     _abi.check(st, "ss_shadow_greedy")
     return {"light": light, "cost": cost, "t_star": t_star}
+
+
+# ---------------------------------------------------------- shading epilogue
+def ss_shade(hf: Heightfield, lights, uv=None, out=None, stream=None):
+    """Lambertian irradiance sum_l I_l s_l max(0, N . L_l) per ray.
+    ``lights``: sequence of (elevation_rad, azimuth_rad, intensity, lit) with
+    ``lit`` the float32 CUDA lit fractions of that light (ss_shadow_forward's light)."""
+    L = _abi.lib()
+    rays, n = _rays(hf, uv, None)
+    arr = (_abi.SSLight * len(lights))()
+    keep = []
+    for k, (e, a, inten, lit) in enumerate(lights):
+        if not (lit.is_cuda and lit.dtype == torch.float32 and lit.is_contiguous()
+                and lit.numel() == n):
+            raise ValueError("lit fractions must be contiguous float32 CUDA tensors [n rays]")
+        keep.append(lit)
+        arr[k] = _abi.SSLight(float(e), float(a), float(inten), lit.data_ptr())
+    E = out if out is not None else torch.empty(n, dtype=torch.float32, device=hf.h.device)
+    st = L.ss_shade(ctypes.byref(hf.c()), ctypes.byref(rays), ctypes.cast(arr, ctypes.c_void_p),
+                    len(lights), _ptr(E), _stream_ptr(stream))
+    _abi.check(st, "ss_shade")
+    return E

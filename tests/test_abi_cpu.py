@@ -202,3 +202,18 @@ def test_greedy_rejects_bad_levels(levels, expect):
                               None, None, None, None)
     # valid levels pass validation and then need an output pointer
     assert st == (1 if expect is None else expect)
+
+
+def test_shade_rejects_bad_lights():
+    lib = _abi.lib()
+    hf, sun, prm, rays, out = _good()
+    good = _abi.SSLight(0.1, 0.2, 1.0, FAKE)
+    for n, lights, expect in ((0, [good], 1), (9, [good] * 9, 1),
+                              (1, [_abi.SSLight(2.0, 0.2, 1.0, FAKE)], 1),
+                              (1, [_abi.SSLight(0.1, float("nan"), 1.0, FAKE)], 1),
+                              (1, [_abi.SSLight(0.1, 0.2, 1.0, None)], 1),
+                              (2, [good, good], 1)):          # valid: then NULL output
+        arr = (_abi.SSLight * len(lights))(*lights)
+        st = lib.ss_shade(ctypes.byref(hf), ctypes.byref(rays), ctypes.cast(arr, ctypes.c_void_p),
+                          n, None, None)
+        assert st == expect

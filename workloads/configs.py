@@ -145,3 +145,11 @@ def camera(width=None, height=None, radius=MOON_RADIUS_M):
     tan_x = tan_y * W / H
     return dict(pos=pos, forward=fwd, right=right, up=up, tan_x=tan_x, tan_y=tan_y,
                 width=W, height=H, step_m=c["step_m"], max_dist_m=c["max_dist_m"])
+
+
+# Lights of the shading epilogue (Sec. 3.4: Sun and Earth as discs).  Sun:
+# the config's sun, unit intensity.  Earth as seen from a lunar pole: low over
+# the horizon, apparent radius 0.95 deg (6371 km at 384,400 km), earthshine
+# irradiance ~1/5000 of sunlight (proposed values).
+EARTH_LIGHT = dict(elevation_deg=2.0, azimuth_deg=0.0, angular_radius_deg=0.95,
+                   intensity=2e-4)
