@@ -119,16 +119,27 @@ typedef struct {
     int32_t leaf_level;    /* forward: subtrees of <= 2^leaf_level samples are
                               evaluated sample by sample; -1 = default (2)     */
     int32_t rays_per_thread; /* forward kernels: a block owns block_threads x
-                              rays_per_thread consecutive rays, in [0, 4096];
-                              0 = default (16)                                 */
+                              rays_per_thread rays, in [0, 4096]; 0 = default
+                              (exact descent 32, otherwise 16)                 */
     int32_t refill_min;    /* forward kernels: a warp's idle lanes take new
                               rays once at least this many are idle, in
-                              [0, 32]; 0 = default (8)                         */
-    int32_t ray_tile_w;    /* grid-mode rays: 0 = a block (batch: a warp) takes
-                              runs of consecutive ray ids; w > 0 = rectangles
-                              of w x (rays / w) texels (w must divide the
-                              block's or chunk's ray count)                   */
-    int32_t reserved;      /* must be 0                                        */
+                              [0, 32]; 0 = default (exact descent 8, else 6)   */
+    int32_t ray_tile_w;    /* grid-mode rays: w > 0 = a block's rays form
+                              rectangles of w x (rays / w) texels (w must
+                              divide the block's or chunk's ray count);
+                              0 = default: 32-wide rectangles for the exact
+                              descent, runs of consecutive ray ids otherwise
+                              (batch: a warp's chunk)                          */
+    int32_t strip_len;     /* ss_shadow_forward (descent): each lane walks a
+                              strip of this many neighbouring rays, and each
+                              ray's descent starts from the best of its own
+                              samples next to the previous ray's argmin (a
+                              sample cost: an upper bound of the minimum, so
+                              results are unchanged); grid rays in rectangles
+                              (ray_tile_w > 0) run down a rectangle column,
+                              other rays take consecutive ids.  In [0, 256];
+                              0 = default (10; light-only mode 1), 1 = no
+                              seeding.  Other calls ignore it.                 */
 } ss_params;
 
 /* Ray origins p (Sec. 3.1: view-ray intersection points). */

@@ -50,9 +50,57 @@ __device__ __forceinline__ int32_t draw(const ChunkRange& P, int32_t* s_next, in
     return my < P.cnt ? my : -1;
 }
 
+// Draw strips for this warp's lanes with r < 0 (one shared-memory atomic per
+// warp); returns the new strip index or -1.
+__device__ __forceinline__ int32_t draw_strip(int32_t n_strips, int32_t* s_next, int32_t r,
+                                              bool& open) {
+    const unsigned idle = __ballot_sync(kFull, r < 0);
+    const int nidle = __popc(idle);
+    int base = 0;
+    if ((threadIdx.x & 31) == 0 && nidle > 0) base = atomicAdd(s_next, nidle);
+    base = __shfl_sync(kFull, base, 0);
+    if (base + nidle >= n_strips) open = false;
+    if (r >= 0) return -1;
+    const int my = base + __popc(idle & lanemask_lt());
+    return my < n_strips ? my : -1;
+}
+
 // ---------------------------------------------------------------- descent
+// Strips: the block's rays are cut into strips of a.strip neighbouring rays
+// (down a column of the block's rectangle for rectangular grid chunks, else
+// consecutive ids).  A lane walks its strip's rays in order; each ray after
+// the first starts its descent with best = the lowest of its own samples
+// within +-kSeedWidth of the previous ray's argmin.  Neighbouring rays are
+// parallel and one texel apart, so their minima sit at nearly the same sample
+// and the walk prunes from the start (a seed is a sample cost, an upper bound
+// of the minimum, so the result is unchanged).
+struct Strip {
+    int32_t first, count;
+};
+
+__device__ __forceinline__ int32_t strip_count(const ChunkRange& P, int32_t S) {
+    if (!P.rect) return (P.cnt + S - 1) / S;
+    const int32_t h = P.cnt / P.w;
+    return P.w * ((h + S - 1) / S);
+}
+
+__device__ __forceinline__ Strip strip_of(const ChunkRange& P, int32_t S, int32_t s) {
+    Strip st;
+    if (!P.rect) {
+        st.first = s * S;
+        st.count = min(S, P.cnt - st.first);
+    } else {
+        const int32_t h = P.cnt / P.w, c = s % P.w, b = s / P.w;
+        st.first = b * S * P.w + c;
+        st.count = min(S, h - b * S);
+    }
+    return st;
+}
+
 // Each loop iteration is one probe of the exact descent (walk_step) per
-// walking lane.
+// walking lane.  Lanes whose ray is done wait until refill_min of them are
+// (or all are); the warp then writes their results and sets up their next
+// rays together (next ray of the strip, or a new strip from the block pool).
 template <bool kCount, bool kGrid, bool kPoly, bool kLight, bool kStereo>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(const FwdArgs a) {
     __shared__ LevelTab s_lev;
@@ -65,8 +113,12 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
     __syncthreads();
     const float span = a.stats[0] - a.stats[1];
     const int32_t kleaf = a.kleaf, levels = a.P.levels;
+    const int32_t S = a.strip;
+    const int32_t n_strips = strip_count(P, S);
 
-    int32_t r = -1;
+    const int32_t stride = P.rect ? P.w : 1;   // local index step along a strip
+    int32_t r = -1;              // local index of the current ray, -1 = none
+    int32_t left = 0;            // rays of the strip after the current one
     bool done = false, open = true;
     RayF rf;
     Walk w;
@@ -74,27 +126,49 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
     w.bestj = -1;
     while (true) {
         unsigned act = __ballot_sync(kFull, r >= 0 && !done);
-        if (act == 0 || (open && __popc(~act) >= a.refill_min)) {
+        const unsigned want = __ballot_sync(kFull, (r < 0 || done) && (left > 0 || open));
+        if (act == 0 || __popc(want) >= a.refill_min) {
+            bool fresh = false;
+            int32_t prev_j = -1;     // argmin of the strip's previous ray
             if (done) {
-                finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj, w.nb, w.nl);
-                r = -1;
+                finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
+                                    w.nb, w.nl);
                 done = false;
+                if (left > 0) {
+                    prev_j = w.bestj;
+                    r += stride;
+                    --left;
+                    fresh = true;
+                } else {
+                    r = -1;
+                }
             }
             if (open) {
-                const int32_t nr = draw(P, &s_next, r, open);
-                if (nr >= 0 && r < 0) {
-                    r = nr;
-                    setup_ray<kGrid, kLight, kStereo>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
-                    walk_begin<kLight>(w, rf, kleaf);
-                    if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
-                        finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj, 0, 0);
-                        r = -1;
-                    }
+                const int32_t ns = draw_strip(n_strips, &s_next, r, open);
+                if (ns >= 0 && r < 0) {
+                    const Strip st = strip_of(P, S, ns);
+                    r = st.first;
+                    left = st.count - 1;
+                    fresh = true;
                 }
+            }
+            if (fresh) {
+                setup_ray<kGrid, kLight, kStereo>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
+                int32_t sj = -1;
+                float sc = INFINITY;
+                if (prev_j > 0) sc = seed_near<kGrid, kPoly, kStereo>(a.T, rf, prev_j, sj);
+                if (sj > 0) {
+                    walk_begin_seeded<kLight>(w, rf, kleaf, sc, sj);
+                    if (kCount) w.nl = min(rf.j_hi, prev_j + kSeedWidth) -
+                                       max(rf.j_lo, prev_j - kSeedWidth) + 1;
+                } else {
+                    walk_begin<kLight>(w, rf, kleaf);
+                }
+                if (rf.j_hi < rf.j_lo) done = true;   // no usable sample: written next service
             }
             act = __ballot_sync(kFull, r >= 0 && !done);
             if (act == 0) {
-                if (!open) break;
+                if (!__any_sync(kFull, (r >= 0) || left > 0) && !open) break;
                 continue;
             }
         }

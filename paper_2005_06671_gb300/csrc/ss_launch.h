@@ -33,6 +33,7 @@ struct FwdArgs {
     int32_t refill_min;       // waiting lanes that trigger a warp service
     int32_t poly;             // 1: the rise series is valid for every ray
     int32_t tile_w;           // grid mode: ray-rectangle width (0 = row-major runs)
+    int32_t strip;            // descent: rays per strip (1 = no seeding)
 };
 
 struct BwdArgs {

@@ -178,6 +178,41 @@ __device__ __forceinline__ void walk_begin(Walk& w, const RayF& rf, int32_t klea
     }
 }
 
+// Seeded start: best is already the cost of sample seed_j (an upper bound of
+// the minimum), so pruning works from the root; the walk still visits every
+// sample whose cost could be lower or equal at a smaller index.
+template <bool kLight = false>
+__device__ __forceinline__ void walk_begin_seeded(Walk& w, const RayF& rf, int32_t kleaf,
+                                                  float seed, int32_t seed_j) {
+    w.s0 = w.nb = w.nl = 0;
+    const int32_t K = rf.j_hi <= 1 ? 0 : 32 - __clz(rf.j_hi - 1);   // 2^K >= j_hi
+    w.k = K > kleaf ? K : 0;
+    const bool use = !kLight || seed < rf.c_sat;
+    w.best = use ? seed : rf.c_sat;
+    w.bestj = use ? seed_j : -1;
+}
+
+// Best of the ray's own samples within +-kSeedWidth of index j0 (clipped to
+// [j_lo, j_hi]); j_out = -1 when none is usable.  Smallest index on ties.
+constexpr int32_t kSeedWidth = 2;
+
+template <bool kGrid, bool kPoly, bool kStereo>
+__device__ __forceinline__ float seed_near(const Tile& T, const RayF& rf, int32_t j0,
+                                           int32_t& j_out) {
+    float best = INFINITY;
+    j_out = -1;
+    const int32_t lo = max(rf.j_lo, j0 - kSeedWidth), hi = min(rf.j_hi, j0 + kSeedWidth);
+    for (int32_t j = lo; j <= hi; ++j) {
+        float rise;
+        const float c = leaf_cost<kGrid, kPoly, kStereo>(T, rf, j, rise);
+        if (c < best) {
+            best = c;
+            j_out = j;
+        }
+    }
+    return best;
+}
+
 // One probe of the exact descent and the state update; true when finished.
 // Stackless depth-first walk over aligned sample blocks [s0+1, s0+2^k]: a
 // block's bound is compared with the running minimum; blocks that cannot win
@@ -197,7 +232,8 @@ __device__ __forceinline__ bool walk_step(const Tile& T, const LevelTab& L, int3
     ja = valid ? ja : rf.j_lo;
     jb = valid ? jb : rf.j_lo;
     const float v = probe<kGrid, kPoly, kStereo>(T, L, levels, rf, ja, jb, leaf);
-    const bool improve = valid && leaf && (v < w.best);
+    // a seeded walk may meet a sample as good as the seed at a smaller index
+    const bool improve = valid && leaf && (v < w.best || (v == w.best && ja < w.bestj));
     w.best = improve ? v : w.best;
     w.bestj = improve ? ja : w.bestj;
     const bool descend = valid && !leaf && !(v > w.best);

@@ -123,6 +123,32 @@ def test_descent_tuning_knobs_do_not_change_results(leaf_level, block):
     assert np.array_equal(out["cost"].view(np.uint32), ref["cost"].view(np.uint32))
 
 
+@pytest.mark.parametrize("strip,tile_w,rpt", [(1, 0, 0), (3, 0, 0), (10, 32, 32), (33, 16, 8),
+                                               (10, 64, 1), (256, 32, 64), (7, 0, 5)])
+def test_seeded_strips_do_not_change_results(strip, tile_w, rpt):
+    """Seeded strips (each ray's walk starts from the previous ray's argmin) in
+    grid and list mode, strips longer than a rectangle column, odd chunk sizes:
+    the same argmin and cost bits as uniform stepping."""
+    inst = make_instance("diff", n=320)
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][1]
+    sun = (elev, az, inst["alpha"])
+    ref = _run(h, g, sun, inst["lmax"], method="uniform")
+    hf = ss.Heightfield(_dev(h), g, R)
+    mip = ss.ss_build_maxmip(hf)
+    res = ss.ss_shadow_forward(hf, mip, ss.Sun(*sun), inst["lmax"], strip_len=strip,
+                               ray_tile_w=tile_w, rays_per_thread=rpt)
+    assert np.array_equal(res["argmin"].cpu().numpy(), ref["argmin"])
+    assert np.array_equal(res["cost"].cpu().numpy().view(np.uint32), ref["cost"].view(np.uint32))
+    uv = random_origins(5000, 320, 320, seed=strip)
+    uv = uv[np.argsort(uv[:, 1] * 400 + uv[:, 0])]          # neighbours next to each other
+    a = ss.ss_shadow_forward(hf, mip, ss.Sun(*sun), inst["lmax"], uv=_dev(uv), strip_len=strip,
+                             rays_per_thread=rpt)
+    b = ss.ss_shadow_uniform(hf, mip, ss.Sun(*sun), inst["lmax"], uv=_dev(uv))
+    assert torch.equal(a["argmin"], b["argmin"])
+    assert torch.equal(a["cost"].view(torch.int32), b["cost"].view(torch.int32))
+
+
 # ------------------------------------------------------------- list mode
 @pytest.mark.parametrize("method", ["dp", "uniform"])
 def test_list_mode_with_lift_vs_oracle(method):
