@@ -280,6 +280,8 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
     B.args.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
     B.args.refill_min = params->refill_min > 0 ? params->refill_min : 6;
     B.args.light_only = (params->flags & SS_FLAG_LIGHT_ONLY) ? 1 : 0;
+    B.args.strip = params->strip_len > 0 ? params->strip_len
+                                         : (B.args.light_only ? 1 : kDefaultStrip);
     return SS_OK;
 }
 

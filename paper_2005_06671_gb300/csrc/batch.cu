@@ -7,7 +7,8 @@
 // atomicAdd per chunk and per warp; each warp keeps a copy of its current
 // instance's descriptor in shared memory and walks each ray with the same
 // exact descent as the single-tile forward (walk_step), refilling idle lanes
-// from its chunk.  A warp switches instance only once all its lanes are idle,
+// from its chunk with strips of neighbouring rays, each ray after a strip's
+// first seeded from the previous ray's argmin (as in the single-tile kernel).  A warp switches instance only once all its lanes are idle,
 // so lanes never mix instances.  No device-side wait: the queue is a counter.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -15,6 +16,7 @@
 
 #include "ss_batch.h"
 #include "ss_walk.cuh"
+#include "ss_strip.cuh"
 
 namespace ss {
 
@@ -50,7 +52,8 @@ __device__ __forceinline__ void load_desc(BatchItemDesc* dst, const BatchItemDes
 struct WarpSched {
     ChunkRange C;       // current chunk of `cur`
     int64_t stash;      // a grabbed chunk of another instance, or -1
-    int32_t c_next;     // next undrawn ray of C
+    int32_t c_next;     // next undrawn strip of C
+    int32_t n_strips;   // strips of C
     int32_t cur;        // instance of this warp, or -1
     int32_t open;       // the queue may still have chunks
     float span;         // height span of `cur`
@@ -68,6 +71,7 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
         S.C.cnt = 0;
         S.stash = -1;
         S.c_next = 0;
+        S.n_strips = 0;
         S.cur = -1;
         S.open = 1;
         S.span = 0.0f;
@@ -75,6 +79,7 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
     __syncwarp();
 
     int32_t r = -1;              // index of this lane's ray within S.C, or -1
+    int32_t left = 0;            // rays of this lane's strip after the current one
     bool done = false;
     RayF rf;
     Walk w;
@@ -82,32 +87,58 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
     w.bestj = -1;
     while (true) {
         unsigned act = __ballot_sync(kFull, r >= 0 && !done);
-        if (act == 0 || (S.open && S.stash < 0 && __popc(~act) >= a.refill_min)) {
+        const bool more = S.open || S.stash >= 0 || S.c_next < S.n_strips;
+        const unsigned want = __ballot_sync(kFull, (r < 0 || done) && (left > 0 || more));
+        if (act == 0 || __popc(want) >= a.refill_min) {
+            // finished rays are written; a lane with more rays in its strip moves
+            // to the next one, seeded from this ray's argmin (same instance)
             if (done) {
                 finish_ray(D.T, grid_rays, D.O, chunk_ray(S.C, D.T.nx, r), w.best, w.bestj, w.nb,
                            w.nl);
-                r = -1;
                 done = false;
+                int32_t prev_j = -1;
+                if (left > 0) {
+                    prev_j = w.bestj;
+                    r += S.C.rect ? S.C.w : 1;
+                    --left;
+                } else {
+                    r = -1;
+                }
+                if (r >= 0) {
+                    setup_ray<true, kLight>(D.T, grid_rays, chunk_ray(S.C, D.T.nx, r), S.span, rf);
+                    int32_t sj = -1;
+                    float sc = INFINITY;
+                    if (prev_j > 0)
+                        sc = D.poly ? seed_near<true, true, false>(D.T, rf, prev_j, sj)
+                                    : seed_near<true, false, false>(D.T, rf, prev_j, sj);
+                    if (sj > 0) {
+                        walk_begin_seeded<kLight>(w, rf, a.kleaf, sc, sj);
+                        if (kCount) w.nl = min(rf.j_hi, prev_j + kSeedWidth) -
+                                           max(rf.j_lo, prev_j - kSeedWidth) + 1;
+                    } else {
+                        walk_begin<kLight>(w, rf, a.kleaf);
+                    }
+                    if (rf.j_hi < rf.j_lo) done = true;   // written at the next service
+                }
             }
-            // draw rays for idle lanes, taking chunks from the queue as needed
+            // draw strips for idle lanes, taking chunks from the queue as needed
             while (true) {
                 const unsigned idle = __ballot_sync(kFull, r < 0);
                 if (idle == 0) break;
-                const int32_t c_next = S.c_next, cnt = S.C.cnt;
-                if (c_next < cnt) {
+                const int32_t c_next = S.c_next, nst = S.n_strips;
+                if (c_next < nst) {
                     const int32_t my = c_next + __popc(idle & lanemask_lt());
-                    if (r < 0 && my < cnt) {
-                        r = my;
-                        const int64_t ray = chunk_ray(S.C, D.T.nx, r);
-                        setup_ray<true, kLight>(D.T, grid_rays, ray, S.span, rf);
+                    if (r < 0 && my < nst) {
+                        const Strip st = strip_of(S.C, a.strip, my);
+                        r = st.first;
+                        left = st.count - 1;
+                        setup_ray<true, kLight>(D.T, grid_rays, chunk_ray(S.C, D.T.nx, r), S.span,
+                                                rf);
                         walk_begin<kLight>(w, rf, a.kleaf);
-                        if (rf.j_hi < rf.j_lo) {   // no usable sample: written at once
-                            finish_ray(D.T, grid_rays, D.O, ray, w.best, w.bestj, 0, 0);
-                            r = -1;
-                        }
+                        if (rf.j_hi < rf.j_lo) done = true;   // written at the next service
                     }
                     __syncwarp();
-                    if (lane == 0) S.c_next = min(c_next + __popc(idle), cnt);
+                    if (lane == 0) S.c_next = min(c_next + __popc(idle), nst);
                     __syncwarp();
                     continue;
                 }
@@ -129,7 +160,7 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                 if (item != S.cur) {
                     const bool walking = __ballot_sync(kFull, r >= 0) != 0;
                     __syncwarp();
-                    if (walking) {   // lanes still walk the current instance
+                    if (walking) {   // lanes still walk (or hold results of) the current instance
                         if (lane == 0) S.stash = q;
                         __syncwarp();
                         break;
@@ -145,13 +176,15 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                     S.stash = -1;
                     S.C = chunk_range(q - __ldg(a.chunk_prefix + item), D.n_rays, D.T.nx, D.T.ny,
                                       a.chunk_rays, D.tile_w);
+                    S.n_strips = strip_count(S.C, a.strip);
                     S.c_next = 0;
                 }
                 __syncwarp();
             }
             act = __ballot_sync(kFull, r >= 0 && !done);
             if (act == 0) {
-                if (!S.open && S.stash < 0) break;
+                if (!__any_sync(kFull, r >= 0) && !S.open && S.stash < 0 && S.c_next >= S.n_strips)
+                    break;
                 continue;
             }
         }

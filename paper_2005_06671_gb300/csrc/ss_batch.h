@@ -33,6 +33,7 @@ struct BatchArgs {
     int32_t kleaf;
     int32_t refill_min;
     int32_t light_only;             // SS_FLAG_LIGHT_ONLY
+    int32_t strip;                  // rays per seeded strip (1 = no seeding)
 };
 
 constexpr size_t kBatchHeader = 256;   // queue counter, padded

@@ -14,6 +14,7 @@
 
 #include "ss_launch.h"
 #include "ss_walk.cuh"
+#include "ss_strip.cuh"
 
 namespace ss {
 
@@ -74,29 +75,6 @@ __device__ __forceinline__ int32_t draw_strip(int32_t n_strips, int32_t* s_next,
 // parallel and one texel apart, so their minima sit at nearly the same sample
 // and the walk prunes from the start (a seed is a sample cost, an upper bound
 // of the minimum, so the result is unchanged).
-struct Strip {
-    int32_t first, count;
-};
-
-__device__ __forceinline__ int32_t strip_count(const ChunkRange& P, int32_t S) {
-    if (!P.rect) return (P.cnt + S - 1) / S;
-    const int32_t h = P.cnt / P.w;
-    return P.w * ((h + S - 1) / S);
-}
-
-__device__ __forceinline__ Strip strip_of(const ChunkRange& P, int32_t S, int32_t s) {
-    Strip st;
-    if (!P.rect) {
-        st.first = s * S;
-        st.count = min(S, P.cnt - st.first);
-    } else {
-        const int32_t h = P.cnt / P.w, c = s % P.w, b = s / P.w;
-        st.first = b * S * P.w + c;
-        st.count = min(S, h - b * S);
-    }
-    return st;
-}
-
 // Each loop iteration is one probe of the exact descent (walk_step) per
 // walking lane.  Lanes whose ray is done wait until refill_min of them are
 // (or all are); the warp then writes their results and sets up their next

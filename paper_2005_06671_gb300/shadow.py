@@ -258,7 +258,7 @@ class Batch:
 
     def __init__(self, hfs, suns, max_len_m, step_texels=0.5, count_samples=False,
                  want_cost=False, block_threads=0, leaf_level=-1, rays_per_thread=0,
-                 refill_min=0, ray_tile_w=0, light_only=False):
+                 refill_min=0, ray_tile_w=0, light_only=False, strip_len=0):
         if len(hfs) != len(suns) or not hfs:
             raise ValueError("need one sun per heightfield, at least one item")
         self.hfs, self.suns = list(hfs), list(suns)
@@ -266,7 +266,7 @@ class Batch:
         flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (SS_FLAG_LIGHT_ONLY if light_only else 0)
         self.params = SSParams(float(max_len_m), float(step_texels), int(flags), int(block_threads),
                                int(leaf_level), int(rays_per_thread), int(refill_min),
-                               int(ray_tile_w), 0)
+                               int(ray_tile_w), int(strip_len))
         n = len(hfs)
         self.items = (_abi.SSBatchItem * n)()
         self.mips, self.outs = [], []

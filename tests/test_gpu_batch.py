@@ -63,7 +63,9 @@ def _same(a, b):
 
 @pytest.mark.parametrize("kw", [dict(), dict(rays_per_thread=4, ray_tile_w=32),
                                 dict(rays_per_thread=2, ray_tile_w=8, refill_min=4),
-                                dict(block_threads=128, leaf_level=3)])
+                                dict(block_threads=128, leaf_level=3),
+                                dict(strip_len=1), dict(strip_len=7, ray_tile_w=16),
+                                dict(strip_len=64, rays_per_thread=8, ray_tile_w=32)])
 def test_batch_equals_single_forward(kw):
     insts = _instances()
     lmax = 2500.0
@@ -75,10 +77,10 @@ def test_batch_equals_single_forward(kw):
 def test_plan_replays_repeat_results_and_count_probes():
     insts = _instances()
     lmax = 2500.0
-    runs = _batch(insts, lmax, plan=True, replays=3, count_samples=True)
+    # without seeded strips every ray is walked from scratch in both kernels, so
+    # the probe counts match too
+    runs = _batch(insts, lmax, plan=True, replays=3, count_samples=True, strip_len=1)
     for (h, g, sun), a, b, c in zip(insts, *runs):
-        # the batch walks every ray unseeded: compare probe counts with the
-        # single-tile descent without strips
         ref = _single(h, g, sun, lmax, count_samples=True, strip_len=1)
         _same(a, ref)
         _same(b, ref)
