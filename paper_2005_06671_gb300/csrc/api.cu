@@ -115,6 +115,9 @@ ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, doubl
     T.delta_f = (float)delta;
     T.inv_delta_f = (float)(1.0 / delta);
     T.sz_f = (float)s[2];
+    T.sx_f = (float)s[0];
+    T.sy_f = (float)s[1];
+    T.R_f = (float)hf->radius_m;
     T.alpha_f = (float)sun->angular_radius_rad;
     return T;
 }
@@ -190,8 +193,13 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     // single rays from row-major runs.
     const bool strips = kind == FwdKind::Descent && !light_only;
     int block = params->block_threads ? params->block_threads : 256;
-    a.rays_per_block = (int64_t)block * (params->rays_per_thread > 0 ? params->rays_per_thread
-                                                                      : (strips ? 32 : 16));
+    int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : (strips ? 32 : 16);
+    if (params->rays_per_thread == 0) {
+        // smaller chunks when the launch would not give every SM a few blocks
+        const int64_t want = (int64_t)ss::device_sm_count() * 8;
+        while (rpt > 4 && (n + (int64_t)block * rpt - 1) / ((int64_t)block * rpt) < want) rpt /= 2;
+    }
+    a.rays_per_block = (int64_t)block * rpt;
     a.refill_min = params->refill_min > 0 ? params->refill_min : (strips ? 8 : 6);
     a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
     a.tile_w = params->ray_tile_w;

@@ -51,6 +51,7 @@ struct Tile {
     float inv_delta_f;         // (float)(1/delta)
     float sz_f;                // (float)sz
     float alpha_f;
+    float sx_f, sy_f, R_f;     // (float)sx, (float)sy, (float)R
 };
 
 struct Rays {
@@ -294,6 +295,95 @@ __device__ __forceinline__ void sample_range(const Tile& T, const Geom64& G, int
 }
 
 // (stereographic tiles only)
+// Exit sample of a ray whose origin lies in the tile (gnomonic): along each
+// axis the image p0 + a j/(1 + b j) leaves [0, n-1] once.  A float32 estimate
+// of the crossing is confirmed (or moved by a step or two) with the exact FP64
+// test  a j <= d (1 + b j)  (a > 0; >= for a < 0; d = bound - p0), which needs
+// no division.  Returns false (caller falls back to sample_range) when the
+// projective denominator could vanish within the ray or the estimate is off.
+__device__ __forceinline__ bool exit_fast(const Tile& T, double up, double vp, double Au,
+                                          double Av, double b, int32_t& j_hi) {
+    const double J = (double)T.J;
+    if (!(1.0 + b * J > 0.25)) return false;   // 1 + b j > 0 on [0, J] (linear in j)
+    int32_t jh = T.J;
+    const double p0s[2] = { up, vp }, as[2] = { Au, Av };
+    const double hi[2] = { (double)(T.nx - 1), (double)(T.ny - 1) };
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double a = as[k];
+        if (a == 0.0) continue;
+        const double d = (a > 0.0 ? hi[k] : 0.0) - p0s[k];
+        const float den = (float)a - (float)b * (float)d;
+        const float jf = den != 0.0f ? (float)d / den : INFINITY;
+        int32_t jc = !(jf < (float)T.J) ? T.J : (jf < 0.0f ? 0 : (int32_t)floorf(jf));
+        // in(j): sample j's image is on the tile side of this bound
+#define SS_IN(j) (a > 0.0 ? (a * (double)(j) <= d * fma(b, (double)(j), 1.0)) \
+                          : (a * (double)(j) >= d * fma(b, (double)(j), 1.0)))
+        int steps = 0;
+        while (jc < T.J && SS_IN(jc + 1) && steps < 3) { ++jc; ++steps; }
+        while (jc >= 1 && !SS_IN(jc) && steps < 3) { --jc; ++steps; }
+        const bool ok = (jc == 0 || SS_IN(jc)) && (jc == T.J || !SS_IN(jc + 1));
+#undef SS_IN
+        if (!ok) return false;
+        jh = min(jh, jc);
+    }
+    j_hi = jh;
+    return true;
+}
+
+// Float32 ray setup for gnomonic tiles.  FP64 only where float32 is not
+// enough: the per-sample slope (a j must be good to ~1e-7 texel at j ~ 10^4)
+// and the usable range; the sun elevation over p and the rise coefficients in
+// float32 (their ~1e-7 errors shift all of a ray's costs together, and rays
+// in the penumbra are re-evaluated in FP64 at the end).
+template <bool kGrid>
+__device__ __forceinline__ void make_rayf_gnomonic(const Tile& T, double up, double vp, float uf,
+                                                   float vf, double hp, double href, float span,
+                                                   RayF& r, float& sin_e) {
+    const double Xp = (up - T.cx) * T.g, Yp = (vp - T.cy) * T.g;
+    const double m2 = Xp * Xp + Yp * Yp + T.R * T.R;
+    const double im = rsqrt(m2);
+    const double rho = T.R + hp;
+    const double f = T.delta * (m2 * im) / rho;
+    const double k = f * T.inv_gR;
+    const double Au = k * (T.R * T.sx - T.sz * Xp), Av = k * (T.R * T.sy - T.sz * Yp);
+    const double b = f * T.sz * T.inv_R;
+    const float Xf = (uf - (float)T.cx) * (float)T.g, Yf = (vf - (float)T.cy) * (float)T.g;
+    const float imf = rsqrtf(Xf * Xf + Yf * Yf + T.R_f * T.R_f);
+    const float se = (Xf * T.sx_f + Yf * T.sy_f + T.R_f * T.sz_f) * imf;
+    const float rhof = T.R_f + (float)hp;
+    sin_e = se;
+    r.iu0 = (int32_t)floorf(uf);
+    r.iv0 = (int32_t)floorf(vf);
+    r.u0 = uf;
+    r.v0 = vf;
+    split8(Au, r.au_hi, r.au_lo);
+    split8(Av, r.av_hi, r.av_lo);
+    r.b = (float)b;
+    r.B = 2.0f * rhof * se;
+    r.inv_2rho = 0.5f / rhof;
+    r.inv_rho2 = 4.0f * r.inv_2rho * r.inv_2rho;
+    r.X = kGrid ? 0.0f : (float)(hp - href);
+    r.href = (float)href;
+    r.tv = se < 0.0f ? -rhof * se : -1.0f;
+    r.guard0 = fabsf(r.X) + span;
+    r.bu = r.bv = r.inv8r = 0.0f;
+    const bool inside = up >= 0.0 && up <= (double)(T.nx - 1) && vp >= 0.0 &&
+                        vp <= (double)(T.ny - 1);
+    r.j_lo = 1;
+    if (!(inside && exit_fast(T, up, vp, Au, Av, b, r.j_hi))) {
+        Geom64 G;
+        G.up = up;
+        G.vp = vp;
+        G.Au = Au;
+        G.Av = Av;
+        G.b = b;
+        sample_range(T, G, r.j_lo, r.j_hi);
+    }
+    const float amax = fmaxf(fabsf(r.au_hi + r.au_lo), fabsf(r.av_hi + r.av_lo));
+    r.pos_eps = 1e-3f + 5e-7f * (float)(T.nx + T.ny) + 8e-7f * amax * (float)max(r.j_hi, 1);
+}
+
 __device__ __forceinline__ bool inside64(const Tile& T, const Geom64& G, int32_t j) {
     double U, V;
     pos64(T, G, (double)j, (double)j * T.delta, U, V, true);
@@ -734,6 +824,12 @@ __device__ __forceinline__ bool texel_image64(const Tile& T, const double x[3], 
 
 __device__ __forceinline__ bool in_tile64(const Tile& T, double u, double v) {
     return u >= 0.0 && u <= (double)(T.nx - 1) && v >= 0.0 && v <= (double)(T.ny - 1);
+}
+
+__device__ __forceinline__ float disc_light32(float d) {
+    if (!(d > -1.0f)) return 0.0f;
+    if (!(d < 1.0f)) return 1.0f;
+    return (3.14159265358979f - acosf(d) + d * sqrtf(1.0f - d * d)) * 0.318309886183791f;
 }
 
 __device__ __forceinline__ double disc_light64(double d) {

@@ -66,8 +66,11 @@ __device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const O
         ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
         Geom64 G;
         geom64_any(T, up, vp, hp, G, kStereo);
-        double c = leaf_cost64(T, G, bestj, kStereo);
-        light = (float)disc_light64(c * cos_elev(G) / T.alpha);
+        // the cost in FP64; the disc formula in float32 (error < 1e-7 in light)
+        const double c = leaf_cost64(T, G, bestj, kStereo);
+        const float se = (float)G.sin_e;
+        const float d = (float)c * sqrtf(fmaxf(0.0f, 1.0f - se * se)) / T.alpha_f;
+        light = disc_light32(d);
         cost = (float)c;
     }
     O.light[r] = light;
@@ -83,8 +86,11 @@ template <bool kGrid, bool kLight = false, bool kStereo = false>
 __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t r, float span,
                                           RayF& rf) {
     double up, vp, hp, href;
+    float uf, vf;
     if (kGrid) {
         const int64_t v = r / T.nx, u = r - v * T.nx;
+        uf = (float)u;
+        vf = (float)v;
         up = (double)u;
         vp = (double)v;
         hp = href = (double)T.h[v * T.pitch + u];
@@ -92,13 +98,20 @@ __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t 
         double ow[4];
         int32_t oi0, oj0;
         ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
+        uf = R.uv[2 * r];
+        vf = R.uv[2 * r + 1];
     }
-    Geom64 G;
-    geom64_any(T, up, vp, hp, G, kStereo);
-    make_rayf<kStereo>(T, G, href, span, rf);
-    if (kGrid) rf.X = 0.0f;
+    float se;
+    if (!kStereo) {
+        make_rayf_gnomonic<kGrid>(T, up, vp, uf, vf, hp, href, span, rf, se);
+    } else {
+        Geom64 G;
+        geom64_stereo(T, up, vp, hp, G);
+        make_rayf<true>(T, G, href, span, rf);
+        if (kGrid) rf.X = 0.0f;
+        se = (float)G.sin_e;
+    }
     if (kLight) {   // saturation threshold of the light (with a 0.2% margin)
-        const float se = (float)G.sin_e;
         const float ce = sqrtf(fmaxf(0.0f, 1.0f - se * se));
         rf.c_sat = ce > 0.0f ? 1.002f * T.alpha_f / ce : INFINITY;
     }
