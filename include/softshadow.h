@@ -123,23 +123,26 @@ typedef struct {
                               (exact descent 32, otherwise 16)                 */
     int32_t refill_min;    /* forward kernels: a warp's idle lanes take new
                               rays once at least this many are idle, in
-                              [0, 32]; 0 = default (exact descent 8, else 6)   */
+                              [0, 32]; 0 = default (exact descent 10, else 6)  */
     int32_t ray_tile_w;    /* grid-mode rays: w > 0 = a block's rays form
                               rectangles of w x (rays / w) texels (w must
                               divide the block's or chunk's ray count);
-                              0 = default: 32-wide rectangles for the exact
+                              0 = default: 256-wide rectangles for the exact
                               descent, runs of consecutive ray ids otherwise
                               (batch: a warp's chunk)                          */
-    int32_t strip_len;     /* ss_shadow_forward (descent): each lane walks a
-                              strip of this many neighbouring rays, and each
-                              ray's descent starts from the best of its own
-                              samples next to the previous ray's argmin (a
-                              sample cost: an upper bound of the minimum, so
-                              results are unchanged); grid rays in rectangles
-                              (ray_tile_w > 0) run down a rectangle column,
-                              other rays take consecutive ids.  In [0, 256];
-                              0 = default (10; light-only mode 1), 1 = no
-                              seeding.  Other calls ignore it.                 */
+    int32_t strip_len;     /* ss_shadow_forward and the batch (exact descent):
+                              seeding of each ray's descent with the best of
+                              its own samples next to a neighbouring ray's
+                              argmin (a sample cost, an upper bound of the
+                              minimum, so results are unchanged).  0 = default:
+                              grid rays in rectangles of <= 1024 columns draw
+                              single rays row by row and seed from the last
+                              finished ray of their column; other rays walk
+                              strips of 10 (light-only mode: no seeding).
+                              S in [2, 256]: each lane walks a strip of S
+                              neighbouring rays (down a rectangle column, or
+                              consecutive ids), seeding from the previous one.
+                              1 = no seeding.  Other calls ignore it.          */
 } ss_params;
 
 /* Ray origins p (Sec. 3.1: view-ray intersection points). */

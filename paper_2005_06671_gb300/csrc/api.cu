@@ -154,6 +154,8 @@ enum class FwdKind { Descent, Uniform };
 
 // default rays per descent strip (each seeded from the previous ray's argmin)
 constexpr int32_t kDefaultStrip = 10;
+// default ray-rectangle width of the exact descent on grid rays
+constexpr int32_t kDefaultTileW = 256;
 
 ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip,
                         const ss_rays* rays, const ss_sun* sun, const ss_params* params,
@@ -187,28 +189,27 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
     a.flags = params->flags;
     const bool light_only = (params->flags & SS_FLAG_LIGHT_ONLY) != 0;
-    // Defaults (measured on GB300, 4096^2 mid workload): the exact descent walks
-    // seeded strips of 10 rays down the columns of 32-wide ray rectangles; the
-    // light-only descent and uniform stepping, whose walks are short, draw
-    // single rays from row-major runs.
+    // Defaults (measured on GB300, 4096^2 mid workload): the exact descent draws
+    // grid rays row by row across 256 x 32 ray rectangles, each seeded from the
+    // last finished ray of its column (listed rays: seeded strips of 10
+    // consecutive ids); the light-only descent and uniform stepping, whose walks
+    // are short, draw single unseeded rays from row-major runs.
     const bool strips = kind == FwdKind::Descent && !light_only;
     int block = params->block_threads ? params->block_threads : 256;
-    int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : (strips ? 32 : 16);
-    if (params->rays_per_thread == 0) {
-        // smaller chunks when the launch would not give every SM a few blocks
-        const int64_t want = (int64_t)ss::device_sm_count() * 8;
-        while (rpt > 4 && (n + (int64_t)block * rpt - 1) / ((int64_t)block * rpt) < want) rpt /= 2;
-    }
+    const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : (strips ? 32 : 16);
     a.rays_per_block = (int64_t)block * rpt;
-    a.refill_min = params->refill_min > 0 ? params->refill_min : (strips ? 8 : 6);
+    a.refill_min = params->refill_min > 0 ? params->refill_min : (strips ? 10 : 6);
     a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
     a.tile_w = params->ray_tile_w;
-    if (a.tile_w == 0 && strips && rays->mode == SS_RAYS_GRID && a.rays_per_block % 32 == 0)
-        a.tile_w = 32;
+    if (a.tile_w == 0 && strips && rays->mode == SS_RAYS_GRID && a.rays_per_block % kDefaultTileW == 0)
+        a.tile_w = kDefaultTileW;
     if (a.tile_w > 0 && a.rays_per_block % a.tile_w != 0) return SS_ERR_INVALID_ARG;
     a.strip = kind == FwdKind::Descent
                   ? (params->strip_len > 0 ? params->strip_len : (light_only ? 1 : kDefaultStrip))
                   : 1;
+    // default for grid rays: single rays with column seeds (no strips)
+    a.colseed = (strips && params->strip_len == 0 && rays->mode == SS_RAYS_GRID && a.tile_w > 0 &&
+                 a.tile_w <= ss::kColSeedMaxW) ? 1 : 0;
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);

@@ -67,6 +67,12 @@ __device__ __forceinline__ int32_t draw_strip(int32_t n_strips, int32_t* s_next,
 }
 
 // ---------------------------------------------------------------- descent
+// Column seeds (grid rays in rectangles of at most kColSeedMaxW columns, the
+// default): lanes draw single rays row by row across the block's rectangle and
+// each ray starts from the lowest of its own samples near the argmin of the
+// last finished ray of its column (a shared-memory table), typically one or two
+// rows above.  Single-ray draws keep the block's tail to one ray per lane.
+//
 // Strips: the block's rays are cut into strips of a.strip neighbouring rays
 // (down a column of the block's rectangle for rectangular grid chunks, else
 // consecutive ids).  A lane walks its strip's rays in order; each ray after
@@ -87,11 +93,15 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
         s_lev.ptr[threadIdx.x] = a.P.ptr[threadIdx.x];
         s_lev.pitch[threadIdx.x] = (uint32_t)a.P.pitch[threadIdx.x];
     }
+    __shared__ int32_t s_seed[kColSeedMaxW];   // column seeds: argmin of a finished ray
     const ChunkRange P = block_pool(a, &s_next);
+    const bool colseed = a.colseed && P.rect;
+    if (colseed)
+        for (int i = threadIdx.x; i < P.w; i += blockDim.x) s_seed[i] = -1;
     __syncthreads();
     const float span = a.stats[0] - a.stats[1];
     const int32_t kleaf = a.kleaf, levels = a.P.levels;
-    const int32_t S = a.strip;
+    const int32_t S = colseed ? 1 : a.strip;
     const int32_t n_strips = strip_count(P, S);
 
     const int32_t stride = P.rect ? P.w : 1;   // local index step along a strip
@@ -111,6 +121,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
             if (done) {
                 finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
                                     w.nb, w.nl);
+                if (colseed && w.bestj > 0) s_seed[r % P.w] = w.bestj;
                 done = false;
                 if (left > 0) {
                     prev_j = w.bestj;
@@ -128,6 +139,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
                     r = st.first;
                     left = st.count - 1;
                     fresh = true;
+                    if (colseed) prev_j = s_seed[r % P.w];   // a ray above in this column
                 }
             }
             if (fresh) {

@@ -34,7 +34,10 @@ struct FwdArgs {
     int32_t poly;             // 1: the rise series is valid for every ray
     int32_t tile_w;           // grid mode: ray-rectangle width (0 = row-major runs)
     int32_t strip;            // descent: rays per strip (1 = no seeding)
+    int32_t colseed;          // descent, grid rays in rectangles: column seeds
 };
+
+constexpr int32_t kColSeedMaxW = 1024;   // widest rectangle with a column-seed table
 
 struct BwdArgs {
     Tile T;
