@@ -6,7 +6,8 @@ Searches, by coordinate descent from the library defaults, over
   ray_tile_w      chunk shape: 0 = runs of consecutive texels, w = w x (rays/w) rectangles
   refill_min      idle lanes that trigger a warp refill
   leaf_level      smallest bounded block = 2^(leaf_level+1) samples
-  strip_len       rays per seeded strip (1 = every ray walked from scratch)
+  strip_len       0 = single rays with column seeds, S = seeded strips of S
+                  rays, 1 = every ray walked from scratch
 timing each candidate as CUDA-event-timed replays of a captured batch plan, and
 keeps the best per (GPU name, tile-size class) in a JSON table.  Every candidate
 gives the same outputs (the descent is exact); only the time changes.
@@ -28,10 +29,10 @@ SPACE = {
     "ray_tile_w": (0, 16, 32, 64),
     "refill_min": (4, 8, 12),
     "leaf_level": (2, 3),
-    "strip_len": (1, 6, 10, 16),
+    "strip_len": (0, 1, 6, 10, 16),
 }
-DEFAULT = {"block_threads": 256, "rays_per_thread": 16, "ray_tile_w": 32, "refill_min": 8,
-           "leaf_level": 2, "strip_len": 10}
+DEFAULT = {"block_threads": 256, "rays_per_thread": 16, "ray_tile_w": 32, "refill_min": 10,
+           "leaf_level": 2, "strip_len": 0}
 
 
 def default_table_path():

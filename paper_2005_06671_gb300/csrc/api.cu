@@ -291,6 +291,7 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
     B.args.light_only = (params->flags & SS_FLAG_LIGHT_ONLY) ? 1 : 0;
     B.args.strip = params->strip_len > 0 ? params->strip_len
                                          : (B.args.light_only ? 1 : kDefaultStrip);
+    B.args.colseed = (params->strip_len == 0 && !B.args.light_only && tile_w > 0) ? 1 : 0;
     return SS_OK;
 }
 

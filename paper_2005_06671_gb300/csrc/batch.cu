@@ -7,8 +7,10 @@
 // atomicAdd per chunk and per warp; each warp keeps a copy of its current
 // instance's descriptor in shared memory and walks each ray with the same
 // exact descent as the single-tile forward (walk_step), refilling idle lanes
-// from its chunk with strips of neighbouring rays, each ray after a strip's
-// first seeded from the previous ray's argmin (as in the single-tile kernel).  A warp switches instance only once all its lanes are idle,
+// from its chunk: by default ray by ray row-major over a rectangular chunk,
+// each ray seeded from the argmin of its column's last finished ray (a small
+// per-warp table), or with strips of neighbouring rays (as in the single-tile
+// kernel).  A warp switches instance only once all its lanes are idle,
 // so lanes never mix instances.  No device-side wait: the queue is a counter.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -54,6 +56,7 @@ struct WarpSched {
     int64_t stash;      // a grabbed chunk of another instance, or -1
     int32_t c_next;     // next undrawn strip of C
     int32_t n_strips;   // strips of C
+    int32_t colseed;    // C is drawn ray by ray with column seeds
     int32_t cur;        // instance of this warp, or -1
     int32_t open;       // the queue may still have chunks
     float span;         // height span of `cur`
@@ -66,12 +69,17 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
     BatchItemDesc& D = reinterpret_cast<BatchItemDesc*>(smem)[wid];
     WarpSched& S = reinterpret_cast<WarpSched*>(
         smem + (size_t)(blockDim.x >> 5) * sizeof(BatchItemDesc))[wid];
+    // column seeds of this warp's chunk: argmin of the last finished ray per column
+    int32_t* seeds = reinterpret_cast<int32_t*>(
+        smem + (size_t)(blockDim.x >> 5) * (sizeof(BatchItemDesc) + sizeof(WarpSched))) +
+        wid * kBatchSeedW;
     const Rays grid_rays = { 0, 0, nullptr, nullptr };
     if (lane == 0) {
         S.C.cnt = 0;
         S.stash = -1;
         S.c_next = 0;
         S.n_strips = 0;
+        S.colseed = 0;
         S.cur = -1;
         S.open = 1;
         S.span = 0.0f;
@@ -95,6 +103,7 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
             if (done) {
                 finish_ray(D.T, grid_rays, D.O, chunk_ray(S.C, D.T.nx, r), w.best, w.bestj, w.nb,
                            w.nl);
+                if (S.colseed && w.bestj > 0) seeds[r % S.C.w] = w.bestj;
                 done = false;
                 int32_t prev_j = -1;
                 if (left > 0) {
@@ -129,12 +138,24 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                 if (c_next < nst) {
                     const int32_t my = c_next + __popc(idle & lanemask_lt());
                     if (r < 0 && my < nst) {
-                        const Strip st = strip_of(S.C, a.strip, my);
+                        const Strip st = strip_of(S.C, S.colseed ? 1 : a.strip, my);
                         r = st.first;
                         left = st.count - 1;
                         setup_ray<true, kLight>(D.T, grid_rays, chunk_ray(S.C, D.T.nx, r), S.span,
                                                 rf);
-                        walk_begin<kLight>(w, rf, a.kleaf);
+                        const int32_t pj = S.colseed ? seeds[r % S.C.w] : -1;
+                        int32_t sj = -1;
+                        float sc = INFINITY;
+                        if (pj > 0)
+                            sc = D.poly ? seed_near<true, true, false>(D.T, rf, pj, sj)
+                                        : seed_near<true, false, false>(D.T, rf, pj, sj);
+                        if (sj > 0) {
+                            walk_begin_seeded<kLight>(w, rf, a.kleaf, sc, sj);
+                            if (kCount) w.nl = min(rf.j_hi, pj + kSeedWidth) -
+                                               max(rf.j_lo, pj - kSeedWidth) + 1;
+                        } else {
+                            walk_begin<kLight>(w, rf, a.kleaf);
+                        }
                         if (rf.j_hi < rf.j_lo) done = true;   // written at the next service
                     }
                     __syncwarp();
@@ -176,9 +197,11 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                     S.stash = -1;
                     S.C = chunk_range(q - __ldg(a.chunk_prefix + item), D.n_rays, D.T.nx, D.T.ny,
                                       a.chunk_rays, D.tile_w);
-                    S.n_strips = strip_count(S.C, a.strip);
+                    S.colseed = a.colseed && S.C.rect && S.C.w <= kBatchSeedW;
+                    S.n_strips = strip_count(S.C, S.colseed ? 1 : a.strip);
                     S.c_next = 0;
                 }
+                for (int i = lane; i < kBatchSeedW; i += 32) seeds[i] = -1;
                 __syncwarp();
             }
             act = __ballot_sync(kFull, r >= 0 && !done);
@@ -223,7 +246,8 @@ void batch_layout(void* ws, int32_t n_items, unsigned long long** counter, Batch
 }
 
 cudaError_t launch_batch_forward(const BatchArgs& a, int block, bool count, cudaStream_t s) {
-    const size_t smem = (size_t)(block / 32) * (sizeof(BatchItemDesc) + sizeof(WarpSched));
+    const size_t smem = (size_t)(block / 32) *
+                        (sizeof(BatchItemDesc) + sizeof(WarpSched) + kBatchSeedW * sizeof(int32_t));
     if (count) {
         if (a.light_only)
             batch_dp_kernel<true, true><<<resident_blocks(batch_dp_kernel<true, true>, block, smem), block, smem, s>>>(a);

@@ -34,7 +34,10 @@ struct BatchArgs {
     int32_t refill_min;
     int32_t light_only;             // SS_FLAG_LIGHT_ONLY
     int32_t strip;                  // rays per seeded strip (1 = no seeding)
+    int32_t colseed;                // rectangular chunks: single rays, column seeds
 };
+
+constexpr int32_t kBatchSeedW = 64;    // widest chunk with a column-seed table
 
 constexpr size_t kBatchHeader = 256;   // queue counter, padded
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
