@@ -192,14 +192,18 @@ __device__ __forceinline__ void walk_begin(Walk& w, const RayF& rf, int32_t klea
 }
 
 // Seeded start: best is already the cost of sample seed_j (an upper bound of
-// the minimum), so pruning works from the root; the walk still visits every
-// sample whose cost could be lower or equal at a smaller index.
+// the minimum); the walk still visits every sample whose cost could be lower
+// or equal at a smaller index.  It starts with the first run of leaves, as an
+// unseeded walk does: every block on the left spine contains the first
+// samples, whose bound (divided by the smallest t) is almost never above best,
+// so probing them first would only add failed bounds.  Light-only walks start
+// at the root, where +c_sat can prune a whole lit ray.
 template <bool kLight = false>
 __device__ __forceinline__ void walk_begin_seeded(Walk& w, const RayF& rf, int32_t kleaf,
                                                   float seed, int32_t seed_j) {
     w.s0 = w.nb = w.nl = 0;
     const int32_t K = rf.j_hi <= 1 ? 0 : 32 - __clz(rf.j_hi - 1);   // 2^K >= j_hi
-    w.k = K > kleaf ? K : 0;
+    w.k = (kLight && K > kleaf) ? K : 0;
     const bool use = !kLight || seed < rf.c_sat;
     w.best = use ? seed : rf.c_sat;
     w.bestj = use ? seed_j : -1;
