@@ -89,6 +89,7 @@ struct RayF {
     int32_t iu0, iv0;          // integer part of the origin position
     float u0, v0;              // origin position (exact: integer or the input float)
     float au_hi, au_lo, av_hi, av_lo;  // per-sample slope split so that j*a_hi is exact
+    float au, av;              // au_hi + au_lo, av_hi + av_lo (rounded once)
     float b;                   // projective coefficient
     float B;                   // 2 rho sin_e
     float inv_2rho, inv_rho2;  // 1/(2 rho), 1/rho^2
@@ -96,6 +97,7 @@ struct RayF {
     float href;
     float tv;                  // distance of the lowest ray point (sin_e < 0), else -1
     float guard0;              // |X| + height span of the tile
+    float gconst;              // 2^-19 (guard0 + 2 max|rise bound| over the ray)
     float pos_eps;             // footprint margin covering float32 block-end positions
     float c_sat;               // light-only mode: 1.002 alpha / cos(eps_p)
     float bu, bv;              // stereographic: texels per metre of w (see Geom64)
@@ -128,6 +130,17 @@ __device__ __forceinline__ void split8(double a, float& hi, float& lo) {
     float af = (float)a;
     hi = __int_as_float(__float_as_int(af) & (int)0xFFFF0000u);
     lo = (float)(a - (double)hi);
+}
+
+// Per-ray part of the float32 guard of a block bound: 2^-19 (guard0 + 2 R_max)
+// with R_max >= |t (B + t)| / rho for every t in [0, t(j_hi)] (which bounds
+// both |rise| and rise_bound), with 0.1% slack for its own rounding.
+__device__ __forceinline__ void set_gconst(const Tile& T, RayF& r) {
+    const float tm = (float)max(r.j_hi, 1) * T.delta_f;
+    const float w1 = fabsf(tm * (r.B + tm));
+    const float w2 = r.B < 0.0f ? 0.25f * r.B * r.B : 0.0f;
+    const float rmax = fmaxf(w1, w2) * (2.0f * r.inv_2rho) * 1.001f;
+    r.gconst = kGuardRel * (r.guard0 + 2.0f * rmax);
 }
 
 // Origin height (FP64) of ray r.
@@ -368,6 +381,8 @@ __device__ __forceinline__ void make_rayf_gnomonic(const Tile& T, double up, dou
     r.tv = se < 0.0f ? -rhof * se : -1.0f;
     r.guard0 = fabsf(r.X) + span;
     r.bu = r.bv = r.inv8r = 0.0f;
+    r.au = __fadd_rn(r.au_hi, r.au_lo);
+    r.av = __fadd_rn(r.av_hi, r.av_lo);
     const bool inside = up >= 0.0 && up <= (double)(T.nx - 1) && vp >= 0.0 &&
                         vp <= (double)(T.ny - 1);
     r.j_lo = 1;
@@ -380,8 +395,9 @@ __device__ __forceinline__ void make_rayf_gnomonic(const Tile& T, double up, dou
         G.b = b;
         sample_range(T, G, r.j_lo, r.j_hi);
     }
-    const float amax = fmaxf(fabsf(r.au_hi + r.au_lo), fabsf(r.av_hi + r.av_lo));
+    const float amax = fmaxf(fabsf(r.au), fabsf(r.av));
     r.pos_eps = 1e-3f + 5e-7f * (float)(T.nx + T.ny) + 8e-7f * amax * (float)max(r.j_hi, 1);
+    set_gconst(T, r);
 }
 
 __device__ __forceinline__ bool inside64(const Tile& T, const Geom64& G, int32_t j) {
@@ -530,6 +546,8 @@ __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double
         r.bv = (float)G.Bv;
         r.inv8r = (float)(G.nz_cross * T.g / (16.0 * T.R));
     }
+    r.au = __fadd_rn(r.au_hi, r.au_lo);
+    r.av = __fadd_rn(r.av_hi, r.av_lo);
     // float32 block-end positions u0 + a*tau err by <= ulp(coordinate) plus
     // ~3 ulp of a*tau; the margin takes 4x that, plus 1e-3 texel
     float amax = fmaxf(fabsf((float)G.Au), fabsf((float)G.Av));
@@ -539,6 +557,7 @@ __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double
         const float bmax = fmaxf(fabsf(r.bu), fabsf(r.bv));
         r.pos_eps += 8e-7f * bmax * 2.0f * (float)((double)max(r.j_hi, 1) * T.delta);
     }
+    set_gconst(T, r);
 }
 
 // ------------------------------------------------------------ float32 leaf
@@ -565,13 +584,13 @@ __device__ __forceinline__ float corr_of(const RayF& r, float jf) {
 // mapping: a * corr (gnomonic, corr = j - j/(1 + b j)) or corr itself
 // (stereographic, in texels).  Base clamped to [0, n-2] (the fraction absorbs it).
 template <bool kGrid, bool kStereo>
-__device__ __forceinline__ Pos axis_pos(int32_t i0, float u0, float a_hi, float a_lo,
+__device__ __forceinline__ Pos axis_pos(int32_t i0, float u0, float a_hi, float a_lo, float a,
                                         float corr, float jf, int32_t n) {
     float p = __fmul_rn(jf, a_hi);       // exact: a_hi has <= 8 significant bits
     float kp = floorf(p);
     float fp = __fsub_rn(p, kp);         // exact
     float tail = kStereo ? __fmaf_rn(jf, a_lo, -corr)
-                         : __fmaf_rn(jf, a_lo, -__fmul_rn(__fadd_rn(a_hi, a_lo), corr));
+                         : __fmaf_rn(jf, a_lo, -__fmul_rn(a, corr));
     float s = kGrid ? __fadd_rn(fp, tail)
                     : __fadd_rn(__fadd_rn(__fsub_rn(u0, (float)i0), fp), tail);
     float fs = floorf(s);
@@ -632,7 +651,7 @@ __device__ __forceinline__ void axis_corr(const Tile& T, const RayF& r, float jf
     if (!kStereo) {
         cu = cv = corr_of(r, jf);
     } else {
-        const float au = __fadd_rn(r.au_hi, r.au_lo), av = __fadd_rn(r.av_hi, r.av_lo);
+        const float au = r.au, av = r.av;
         const float w = __fadd_rn(rise, __fmul_rn(t, T.sz_f));
         const float q = __fdividef(w, __fmaf_rn(w, r.b, 1.0f));   // r.b = 1/a0
         cu = __fmul_rn(q, __fmaf_rn(__fmul_rn(jf, au), r.b, r.bu));
@@ -661,8 +680,8 @@ __device__ __forceinline__ float leaf_cost(const Tile& T, const RayF& r, int32_t
     const float rise_s = kStereo ? rise_of<kPoly>(r, t) : 0.0f;
     float cu, cv;
     axis_corr<kStereo>(T, r, jf, t, rise_s, cu, cv);
-    const Pos pu = axis_pos<kGrid, kStereo>(r.iu0, r.u0, r.au_hi, r.au_lo, cu, jf, T.nx);
-    const Pos pv = axis_pos<kGrid, kStereo>(r.iv0, r.v0, r.av_hi, r.av_lo, cv, jf, T.ny);
+    const Pos pu = axis_pos<kGrid, kStereo>(r.iu0, r.u0, r.au_hi, r.au_lo, r.au, cu, jf, T.nx);
+    const Pos pv = axis_pos<kGrid, kStereo>(r.iv0, r.v0, r.av_hi, r.av_lo, r.av, cv, jf, T.ny);
     const uint32_t pitch = (uint32_t)T.pitch;
     const float* p = cell_ptr(T.h, pitch, pu.i, pv.i);
     const float d00 = __fsub_rn(__ldg(p), r.href), d10 = __fsub_rn(__ldg(p + 1), r.href);
@@ -679,7 +698,7 @@ __device__ __forceinline__ float leaf_cost(const Tile& T, const RayF& r, int32_t
 template <bool kStereo>
 __device__ __forceinline__ void block_end(const Tile& T, const RayF& r, float jf, float t,
                                           float rise, float& u, float& v) {
-    const float au = __fadd_rn(r.au_hi, r.au_lo), av = __fadd_rn(r.av_hi, r.av_lo);
+    const float au = r.au, av = r.av;
     if (!kStereo) {
         float tau = __fdividef(jf, __fmaf_rn(jf, r.b, 1.0f));
         u = __fmaf_rn(au, tau, r.u0);
@@ -720,11 +739,12 @@ __device__ __forceinline__ float probe(const Tile& T, const LevelTab& L, int32_t
     // leaf position (the sample's bilinear cell)
     float cu, cv;
     axis_corr<kStereo>(T, r, fa, sa, rise_a, cu, cv);
-    const Pos ua = axis_pos<kGrid, kStereo>(r.iu0, r.u0, r.au_hi, r.au_lo, cu, fa, T.nx);
-    const Pos va = axis_pos<kGrid, kStereo>(r.iv0, r.v0, r.av_hi, r.av_lo, cv, fa, T.ny);
-    // block footprint box from both ends (stereographic: plus the arc's sagitta)
-    float xa, ya, xb, yb;
-    block_end<kStereo>(T, r, fa, sa, rise_a, xa, ya);
+    const Pos ua = axis_pos<kGrid, kStereo>(r.iu0, r.u0, r.au_hi, r.au_lo, r.au, cu, fa, T.nx);
+    const Pos va = axis_pos<kGrid, kStereo>(r.iv0, r.v0, r.av_hi, r.av_lo, r.av, cv, fa, T.ny);
+    // block footprint box from both ends (stereographic: plus the arc's sagitta);
+    // the near end is the leaf position (i + f, more accurate than block_end)
+    const float xa = __fadd_rn((float)ua.i, ua.f), ya = __fadd_rn((float)va.i, va.f);
+    float xb, yb;
     block_end<kStereo>(T, r, fb, sb, kStereo ? rise_of<kPoly>(r, sb) : 0.0f, xb, yb);
     float e = r.pos_eps;
     if (kStereo) {
@@ -760,7 +780,8 @@ __device__ __forceinline__ float probe(const Tile& T, const LevelTab& L, int32_t
                          : fmaxf(fmaxf(d00, d10), fmaxf(d01, d11));
     const float h = kGrid ? rise : __fadd_rn(r.X, rise);
     const float num0 = __fsub_rn(h, V);
-    const float guard = kGuardRel * (r.guard0 + fabsf(V) + rise_bound(r, tb) + fabsf(rise));
+    // |rise| and rise_bound(tb) are both below the ray's largest rise bound
+    const float guard = fmaf(kGuardRel, fabsf(V), r.gconst);
     const float num = leaf ? num0 : __fsub_rn(num0, guard);
     const float den_j = (leaf || !(num >= 0.0f)) ? fa : fb;
     return __fmul_rn(num, inv_t(T, den_j));
