@@ -138,7 +138,7 @@ typedef struct {
                               grid rays in rectangles of <= 1024 columns draw
                               single rays row by row and seed from the last
                               finished ray of their column; other rays walk
-                              strips of 10 (light-only mode: no seeding).
+                              strips of 10 (in light-only mode: no seeding).
                               S in [2, 256]: each lane walks a strip of S
                               neighbouring rays (down a rectangle column, or
                               consecutive ids), seeding from the previous one.

@@ -189,12 +189,13 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
     a.flags = params->flags;
     const bool light_only = (params->flags & SS_FLAG_LIGHT_ONLY) != 0;
-    // Defaults (measured on GB300, 4096^2 mid workload): the exact descent draws
-    // grid rays row by row across 256 x 32 ray rectangles, each seeded from the
-    // last finished ray of its column (listed rays: seeded strips of 10
-    // consecutive ids); the light-only descent and uniform stepping, whose walks
-    // are short, draw single unseeded rays from row-major runs.
-    const bool strips = kind == FwdKind::Descent && !light_only;
+    // Defaults (measured on GB300, 4096^2 mid workload): the descent (exact and
+    // light-only) draws grid rays row by row across 256 x 32 ray rectangles, each
+    // seeded from the last finished ray of its column; listed rays walk seeded
+    // strips of 10 consecutive ids (light-only: single unseeded rays, whose walks
+    // are too short to pay for a strip's tail); uniform stepping draws single
+    // rays from row-major runs.
+    const bool strips = kind == FwdKind::Descent;
     int block = params->block_threads ? params->block_threads : 256;
     const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : (strips ? 32 : 16);
     a.rays_per_block = (int64_t)block * rpt;
