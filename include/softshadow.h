@@ -135,10 +135,12 @@ typedef struct {
                               its own samples next to a neighbouring ray's
                               argmin (a sample cost, an upper bound of the
                               minimum, so results are unchanged).  0 = default:
-                              grid rays in rectangles of <= 1024 columns draw
-                              single rays row by row and seed from the last
-                              finished ray of their column; other rays walk
-                              strips of 10 (in light-only mode: no seeding).
+                              single rays drawn row by row, each seeded from
+                              the last finished ray of its column (grid rays:
+                              columns of the ray rectangle; listed rays: a
+                              block's ids read as 256 columns of consecutive
+                              ids; listed rays in light-only mode: no
+                              seeding).
                               S in [2, 256]: each lane walks a strip of S
                               neighbouring rays (down a rectangle column, or
                               consecutive ids), seeding from the previous one.

@@ -189,12 +189,12 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
     a.flags = params->flags;
     const bool light_only = (params->flags & SS_FLAG_LIGHT_ONLY) != 0;
-    // Defaults (measured on GB300, 4096^2 mid workload): the descent (exact and
-    // light-only) draws grid rays row by row across 256 x 32 ray rectangles, each
-    // seeded from the last finished ray of its column; listed rays walk seeded
-    // strips of 10 consecutive ids (light-only: single unseeded rays, whose walks
-    // are too short to pay for a strip's tail); uniform stepping draws single
-    // rays from row-major runs.
+    // Defaults (measured on GB300: 4096^2 mid workload, polar view): the descent
+    // (exact and light-only) draws grid rays row by row across 256 x 32 ray
+    // rectangles, each seeded from the last finished ray of its column; listed
+    // rays are read as 256 columns of consecutive ids and drawn the same way
+    // (exact mode; light-only listed rays stay unseeded); uniform stepping draws
+    // single rays from row-major runs.
     const bool strips = kind == FwdKind::Descent;
     int block = params->block_threads ? params->block_threads : 256;
     const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : (strips ? 32 : 16);
@@ -208,9 +208,14 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.strip = kind == FwdKind::Descent
                   ? (params->strip_len > 0 ? params->strip_len : (light_only ? 1 : kDefaultStrip))
                   : 1;
-    // default for grid rays: single rays with column seeds (no strips)
-    a.colseed = (strips && params->strip_len == 0 && rays->mode == SS_RAYS_GRID && a.tile_w > 0 &&
-                 a.tile_w <= ss::kColSeedMaxW) ? 1 : 0;
+    // default: single rays with column seeds (no strips); grid rays in rectangles
+    // of at most kColSeedMaxW columns, or runs of ids read as columns
+    // (listed rays in light-only mode stay unseeded: measured faster on the
+    // polar view, whose lit rays end at the root)
+    a.colseed = (strips && params->strip_len == 0 &&
+                 (rays->mode == SS_RAYS_GRID ? (a.tile_w == 0 || a.tile_w <= ss::kColSeedMaxW)
+                                             : !light_only))
+                    ? 1 : 0;
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);

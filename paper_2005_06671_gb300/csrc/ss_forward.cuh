@@ -95,14 +95,19 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
     }
     __shared__ int32_t s_seed[kColSeedMaxW];   // column seeds: argmin of a finished ray
     const ChunkRange P = block_pool(a, &s_next);
-    const bool colseed = a.colseed && P.rect;
+    // Column seeds.  Grid rectangles: columns of the rectangle.  Runs of ids
+    // (listed rays): the run is read as LW columns of LH consecutive ids each,
+    // drawn row by row, so an id is drawn a round after the id before it.
+    const bool colseed = a.colseed != 0;
+    const int32_t LW = (colseed && !P.rect) ? min(kColSeedMaxW / 4, P.cnt) : 0;
+    const int32_t LH = LW > 0 ? (P.cnt + LW - 1) / LW : 0;
     if (colseed)
-        for (int i = threadIdx.x; i < P.w; i += blockDim.x) s_seed[i] = -1;
+        for (int i = threadIdx.x; i < (P.rect ? P.w : LW); i += blockDim.x) s_seed[i] = -1;
     __syncthreads();
     const float span = a.stats[0] - a.stats[1];
     const int32_t kleaf = a.kleaf, levels = a.P.levels;
     const int32_t S = colseed ? 1 : a.strip;
-    const int32_t n_strips = strip_count(P, S);
+    const int32_t n_strips = LW > 0 ? LW * LH : strip_count(P, S);
 
     const int32_t stride = P.rect ? P.w : 1;   // local index step along a strip
     int32_t r = -1;              // local index of the current ray, -1 = none
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
             if (done) {
                 finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
                                     w.nb, w.nl);
-                if (colseed && w.bestj > 0) s_seed[r % P.w] = w.bestj;
+                if (colseed && w.bestj > 0) s_seed[P.rect ? r % P.w : r / LH] = w.bestj;
                 done = false;
                 if (left > 0) {
                     prev_j = w.bestj;
@@ -135,11 +140,21 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
             if (open) {
                 const int32_t ns = draw_strip(n_strips, &s_next, r, open);
                 if (ns >= 0 && r < 0) {
-                    const Strip st = strip_of(P, S, ns);
-                    r = st.first;
-                    left = st.count - 1;
-                    fresh = true;
-                    if (colseed) prev_j = s_seed[r % P.w];   // a ray above in this column
+                    if (LW > 0) {            // virtual column ns % LW, row ns / LW
+                        const int32_t e = (ns % LW) * LH + ns / LW;
+                        if (e < P.cnt) {
+                            r = e;
+                            left = 0;
+                            fresh = true;
+                            prev_j = s_seed[ns % LW];
+                        }
+                    } else {
+                        const Strip st = strip_of(P, S, ns);
+                        r = st.first;
+                        left = st.count - 1;
+                        fresh = true;
+                        if (colseed) prev_j = s_seed[r % P.w];   // a ray above in this column
+                    }
                 }
             }
             if (fresh) {
