@@ -123,12 +123,13 @@ def test_descent_tuning_knobs_do_not_change_results(leaf_level, block):
     assert np.array_equal(out["cost"].view(np.uint32), ref["cost"].view(np.uint32))
 
 
-@pytest.mark.parametrize("strip,tile_w,rpt", [(1, 0, 0), (3, 0, 0), (10, 32, 32), (33, 16, 8),
+@pytest.mark.parametrize("strip,tile_w,rpt", [(0, 0, 0), (0, 32, 3), (0, 0, 7), (1, 0, 0),
+                                               (3, 0, 0), (10, 32, 32), (33, 16, 8),
                                                (10, 64, 1), (256, 32, 64), (7, 0, 5)])
 def test_seeded_strips_do_not_change_results(strip, tile_w, rpt):
-    """Seeded strips (each ray's walk starts from the previous ray's argmin) in
-    grid and list mode, strips longer than a rectangle column, odd chunk sizes:
-    the same argmin and cost bits as uniform stepping."""
+    """Seeded walks (column seeds by default, strip_len 0; strips of S rays;
+    none) in grid and list mode, strips longer than a rectangle column, odd
+    and partial chunks: the same argmin and cost bits as uniform stepping."""
     inst = make_instance("diff", n=320)
     h, g = inst["h"], inst["g"]
     elev, az = inst["suns"][1]
