@@ -51,6 +51,12 @@ __device__ __forceinline__ void load_desc(BatchItemDesc* dst, const BatchItemDes
 
 // Warp-uniform scheduling state, kept in shared memory next to the warp's
 // instance descriptor so the lanes' registers hold only the walk.
+struct LaneRay {
+    int64_t ray;        // the lane's ray: id within the warp's instance
+    int32_t slot;       // its column in the seed table, or -1
+    int32_t pad;
+};
+
 struct WarpSched {
     ChunkRange C;       // current chunk of `cur`
     int64_t stash;      // a grabbed chunk of another instance, or -1
@@ -73,6 +79,14 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
     int32_t* seeds = reinterpret_cast<int32_t*>(
         smem + (size_t)(blockDim.x >> 5) * (sizeof(BatchItemDesc) + sizeof(WarpSched))) +
         wid * kBatchSeedW;
+    // Each lane's ray as an id within the instance, and its seed column: a warp
+    // moves to its next chunk (same instance) while other lanes still walk rays
+    // of the previous one, so a lane's ray must not be kept as an index into
+    // the warp's current chunk.
+    LaneRay& L = reinterpret_cast<LaneRay*>(
+        smem + (size_t)(blockDim.x >> 5) *
+                   (sizeof(BatchItemDesc) + sizeof(WarpSched) + kBatchSeedW * sizeof(int32_t)))
+        [threadIdx.x];
     const Rays grid_rays = { 0, 0, nullptr, nullptr };
     if (lane == 0) {
         S.C.cnt = 0;
@@ -86,7 +100,7 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
     }
     __syncwarp();
 
-    int32_t r = -1;              // index of this lane's ray within S.C, or -1
+    int32_t r = -1;              // >= 0 while this lane holds a ray (id in L.ray)
     int32_t left = 0;            // rays of this lane's strip after the current one
     bool done = false;
     RayF rf;
@@ -101,20 +115,20 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
             // finished rays are written; a lane with more rays in its strip moves
             // to the next one, seeded from this ray's argmin (same instance)
             if (done) {
-                finish_ray(D.T, grid_rays, D.O, chunk_ray(S.C, D.T.nx, r), w.best, w.bestj, w.nb,
-                           w.nl);
-                if (S.colseed && w.bestj > 0) seeds[r % S.C.w] = w.bestj;
+                finish_ray(D.T, grid_rays, D.O, L.ray, w.best, w.bestj, w.nb, w.nl);
+                if (L.slot >= 0 && w.bestj > 0) seeds[L.slot] = w.bestj;
                 done = false;
                 int32_t prev_j = -1;
-                if (left > 0) {
+                if (left > 0) {          // next ray of the strip: a row down, or the next id
                     prev_j = w.bestj;
-                    r += S.C.rect ? S.C.w : 1;
+                    L.ray += D.tile_w > 0 ? (int64_t)D.T.nx : 1;
+                    L.slot = -1;
                     --left;
                 } else {
                     r = -1;
                 }
                 if (r >= 0) {
-                    setup_ray<true, kLight>(D.T, grid_rays, chunk_ray(S.C, D.T.nx, r), S.span, rf);
+                    setup_ray<true, kLight>(D.T, grid_rays, L.ray, S.span, rf);
                     int32_t sj = -1;
                     float sc = INFINITY;
                     if (prev_j > 0)
@@ -141,9 +155,10 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                         const Strip st = strip_of(S.C, S.colseed ? 1 : a.strip, my);
                         r = st.first;
                         left = st.count - 1;
-                        setup_ray<true, kLight>(D.T, grid_rays, chunk_ray(S.C, D.T.nx, r), S.span,
-                                                rf);
-                        const int32_t pj = S.colseed ? seeds[r % S.C.w] : -1;
+                        L.ray = chunk_ray(S.C, D.T.nx, r);
+                        L.slot = S.colseed ? r % S.C.w : -1;
+                        setup_ray<true, kLight>(D.T, grid_rays, L.ray, S.span, rf);
+                        const int32_t pj = S.colseed ? seeds[L.slot] : -1;
                         int32_t sj = -1;
                         float sc = INFINITY;
                         if (pj > 0)
@@ -247,7 +262,8 @@ void batch_layout(void* ws, int32_t n_items, unsigned long long** counter, Batch
 
 cudaError_t launch_batch_forward(const BatchArgs& a, int block, bool count, cudaStream_t s) {
     const size_t smem = (size_t)(block / 32) *
-                        (sizeof(BatchItemDesc) + sizeof(WarpSched) + kBatchSeedW * sizeof(int32_t));
+                            (sizeof(BatchItemDesc) + sizeof(WarpSched) + kBatchSeedW * sizeof(int32_t)) +
+                        (size_t)block * sizeof(LaneRay);
     if (count) {
         if (a.light_only)
             batch_dp_kernel<true, true><<<resident_blocks(batch_dp_kernel<true, true>, block, smem), block, smem, s>>>(a);

@@ -74,6 +74,22 @@ def test_batch_equals_single_forward(kw):
         _same(got, _single(h, g, sun, lmax))
 
 
+@pytest.mark.parametrize("kw", [dict(rays_per_thread=1, refill_min=1, strip_len=1),
+                                dict(rays_per_thread=1, refill_min=2, ray_tile_w=8),
+                                dict(rays_per_thread=3, refill_min=1, strip_len=5, ray_tile_w=32)])
+def test_batch_chunk_switches_keep_every_ray(kw):
+    """Tiny chunks and eager refills: warps move to their next chunk while other
+    lanes still walk rays of the previous one; every ray must still be written
+    with its own result (outputs are pre-filled with sentinels)."""
+    h = lunar_tile(300, 12.0, seed=77, amplitude=700.0, n_craters=6, ny=260)
+    insts = [(h, 12.0, (math.radians(1.1), math.radians(60.0), ALPHA)),
+             (h[:100, :130].copy(), 12.0, (math.radians(0.7), math.radians(250.0), ALPHA))]
+    res = _batch(insts, 3000.0, **kw)[0]
+    for (hh, g, sun), got in zip(insts, res):
+        assert np.all(got["argmin"] != -7) and np.all(got["light"] >= 0.0)
+        _same(got, _single(hh, g, sun, 3000.0))
+
+
 def test_plan_replays_repeat_results_and_count_probes():
     insts = _instances()
     lmax = 2500.0
