@@ -413,7 +413,8 @@ __device__ __forceinline__ bool inside64(const Tile& T, const Geom64& G, int32_t
 // crossing points exactly (a quadratic), each mapped back to its ray distance
 // t = -((p x n) . (s x n)) / |s x n|^2; the run is bounded by the first
 // crossings, then its end samples are confirmed with the FP64 position.
-__device__ __forceinline__ void sample_range_stereo(const Tile& T, const Geom64& G,
+// (kept out of line: its FP64 scratch would otherwise crowd the walk's registers)
+static __device__ __noinline__ void sample_range_stereo(const Tile& T, const Geom64& G,
                                                     int32_t& j_lo, int32_t& j_hi) {
     const double p[3] = { G.rho * G.nhat[0], G.rho * G.nhat[1], G.rho * G.nhat[2] };
     const double sv[3] = { T.sx, T.sy, T.sz };
