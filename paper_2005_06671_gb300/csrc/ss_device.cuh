@@ -328,6 +328,19 @@ __device__ __forceinline__ bool exit_fast(const Tile& T, double up, double vp, d
         const double d = (a > 0.0 ? hi[k] : 0.0) - p0s[k];
         const float den = (float)a - (float)b * (float)d;
         const float jf = den != 0.0f ? (float)d / den : INFINITY;
+        // the float estimate is within ~3e-7 jf of the crossing: when that
+        // leaves no doubt about floor(jf) (or about jf >= J), it is the answer
+        const float margin = 1e-6f * fabsf(jf) + 1e-3f;
+        if (den > 0.0f && jf >= 0.0f) {
+            if (jf >= (float)T.J + margin) {
+                continue;                            // no exit before J on this axis
+            }
+            const float fl = floorf(jf), fr = jf - fl;
+            if (fr > margin && fr < 1.0f - margin && jf < (float)T.J) {
+                jh = min(jh, (int32_t)fl);
+                continue;
+            }
+        }
         int32_t jc = !(jf < (float)T.J) ? T.J : (jf < 0.0f ? 0 : (int32_t)floorf(jf));
         // in(j): sample j's image is on the tile side of this bound
 #define SS_IN(j) (a > 0.0 ? (a * (double)(j) <= d * fma(b, (double)(j), 1.0)) \
@@ -355,9 +368,14 @@ __device__ __forceinline__ void make_rayf_gnomonic(const Tile& T, double up, dou
                                                    RayF& r, float& sin_e) {
     const double Xp = (up - T.cx) * T.g, Yp = (vp - T.cy) * T.g;
     const double m2 = Xp * Xp + Yp * Yp + T.R * T.R;
-    const double im = rsqrt(m2);
+    // 1/sqrt(m2) and 1/rho from float seeds and one Newton step each (relative
+    // error ~1e-14, far below what the positions need; no FP64 division)
+    double im = (double)rsqrtf((float)m2);
+    im = im * fma(-0.5 * m2, im * im, 1.5);
     const double rho = T.R + hp;
-    const double f = T.delta * (m2 * im) / rho;
+    double ir = (double)__frcp_rn((float)rho);
+    ir = ir * fma(-rho, ir, 2.0);
+    const double f = T.delta * (m2 * im) * ir;
     const double k = f * T.inv_gR;
     const double Au = k * (T.R * T.sx - T.sz * Xp), Av = k * (T.R * T.sy - T.sz * Yp);
     const double b = f * T.sz * T.inv_R;
