@@ -239,7 +239,8 @@ def run_ours(args):
                    "rays_per_step": n_rays, "l2": "flushed before every timed step (512 MiB write)",
                    "parallelism": f"replicas x{world} (weak)"},
         "clocks": clocks,
-        "gpu_launches": (mip_passes + 1) * args.steps,
+        # per step: the mipmap passes, the descent and its FP64 refine pass
+        "gpu_launches": (mip_passes + 2) * args.steps,
         "mip_build_ms": statistics.median(mip_ms),
         "forward_ms": statistics.median(fwd_ms),
     }

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
             bool fresh = false;
             int32_t prev_j = -1;     // argmin of the strip's previous ray
             if (done) {
-                finish_ray<kStereo>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
+                finish_ray<kStereo, true>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
                                     w.nb, w.nl);
                 if (colseed && w.bestj > 0) s_seed[P.rect ? r % P.w : r / LH] = w.bestj;
                 done = false;
@@ -262,6 +262,36 @@ static int pool_grid(const FwdArgs& a) {
                             a.R.mode == 0 ? a.tile_w : 0);
 }
 
+// ---------------------------------------------------------------- refine
+// FP64 re-evaluation of the rays the descent left pending (penumbra rays, a
+// few percent).  A block gathers the pending rays of its kRefineRounds x 256
+// ids into shared memory, then every thread takes one: full warps of FP64 work
+// instead of a lane or two inside the walk's services.
+constexpr int kRefineRounds = 8;
+
+template <bool kStereo>
+__global__ void __launch_bounds__(256) refine_kernel(const FwdArgs a) {
+    __shared__ int64_t s_ray[256 * kRefineRounds];
+    __shared__ int32_t s_cnt;
+    const int64_t n = ray_count(a.T, a.R);
+    const int64_t base = (int64_t)blockIdx.x * 256 * kRefineRounds;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int k = 0; k < kRefineRounds; ++k) {
+        const int64_t r = base + (int64_t)k * 256 + threadIdx.x;
+        if (r < n && a.O.light[r] == kLightPending) s_ray[atomicAdd(&s_cnt, 1)] = r;
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int i = threadIdx.x; i < cnt; i += 256) {
+        const int64_t r = s_ray[i];
+        float light, cost;
+        refine_ray(a.T, a.R, r, a.O.argmin[r], kStereo, light, cost);
+        a.O.light[r] = light;
+        if (a.O.cost) a.O.cost[r] = cost;
+    }
+}
+
 #define SS_FWD_CASE(C, G, P, L) \
     case ((C) << 3) | ((G) << 2) | ((P) << 1) | (L): return Launch<C, G, P, L, kStereo>::go(a, grid, block, s);
 
@@ -285,6 +315,9 @@ template <bool C, bool G, bool P, bool L, bool S>
 struct DpLaunch {
     static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
         dp_forward_kernel<C, G, P, L, S><<<grid, block, 0, s>>>(a);
+        const int64_t n = a.R.mode == 0 ? (int64_t)a.T.nx * a.T.ny : a.R.n;
+        const int64_t rb = ((n + 256 * kRefineRounds - 1) / (256 * kRefineRounds));
+        refine_kernel<S><<<(unsigned)rb, 256, 0, s>>>(a);
         return cudaGetLastError();
     }
 };

@@ -46,36 +46,53 @@ __device__ __forceinline__ float cos_elev_f32(const Tile& T, const Rays& R, int6
     return sqrtf(fmaxf(0.0f, 1.0f - se * se));
 }
 
-// Final value of one ray: re-evaluate the argmin sample in FP64 unless the
-// light is certainly saturated (|c*| cos(eps) >= 1.001 alpha), then the
-// disc-occlusion formula (Eq. discfrac).
-template <bool kStereo = false>
+// FP64 re-evaluation of ray r's argmin sample (rays whose light is not
+// saturated): the cost in FP64, the disc formula (Eq. discfrac) in float32
+// (error < 1e-7 in light).
+__device__ __forceinline__ void refine_ray(const Tile& T, const Rays& R, int64_t r,
+                                           int32_t bestj, bool stereo, float& light, float& cost) {
+    double up, vp, hp, href, ow[4];
+    int32_t oi0, oj0;
+    ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
+    Geom64 G;
+    geom64_any(T, up, vp, hp, G, stereo);
+    const double c = leaf_cost64(T, G, bestj, stereo);
+    const float se = (float)G.sin_e;
+    const float d = (float)c * sqrtf(fmaxf(0.0f, 1.0f - se * se)) / T.alpha_f;
+    light = disc_light32(d);
+    cost = (float)c;
+}
+
+// Light value marking a ray whose FP64 re-evaluation is left to refine_kernel.
+constexpr float kLightPending = -1.0f;
+
+// Final value of one ray: the FP64 re-evaluation of its argmin sample unless
+// the light is certainly saturated (|c*| cos(eps) >= 1.001 alpha), then the
+// disc-occlusion formula (Eq. discfrac).  kDefer: leave the re-evaluation to
+// refine_kernel (light = kLightPending), so that the walk's warp services
+// carry no FP64 re-evaluation with a lane or two active.
+template <bool kStereo = false, bool kDefer = false>
 __device__ __forceinline__ void finish_ray(const Tile& T, const Rays& R, const Outputs& O,
                                            int64_t r, float best, int32_t bestj, int32_t nb,
                                            int32_t nl) {
     float light, cost;
+    bool write_cost = true;
     if (bestj < 0) {
         light = 1.0f;
         cost = INFINITY;
     } else if (fabsf(best) * cos_elev_f32(T, R, r, kStereo) >= 1.001f * T.alpha_f) {
         light = best > 0.0f ? 1.0f : 0.0f;
         cost = best;
+    } else if (kDefer) {
+        light = kLightPending;
+        cost = 0.0f;
+        write_cost = false;
     } else {
-        double up, vp, hp, href, ow[4];
-        int32_t oi0, oj0;
-        ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
-        Geom64 G;
-        geom64_any(T, up, vp, hp, G, kStereo);
-        // the cost in FP64; the disc formula in float32 (error < 1e-7 in light)
-        const double c = leaf_cost64(T, G, bestj, kStereo);
-        const float se = (float)G.sin_e;
-        const float d = (float)c * sqrtf(fmaxf(0.0f, 1.0f - se * se)) / T.alpha_f;
-        light = disc_light32(d);
-        cost = (float)c;
+        refine_ray(T, R, r, bestj, kStereo, light, cost);
     }
     O.light[r] = light;
     O.argmin[r] = bestj;
-    if (O.cost) O.cost[r] = cost;
+    if (O.cost && write_cost) O.cost[r] = cost;
     if (O.counters) {
         O.counters[2 * r] = nb;
         O.counters[2 * r + 1] = nl;
