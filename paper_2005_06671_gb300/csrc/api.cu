@@ -152,9 +152,10 @@ bool rise_series_ok(const ss_heightfield* hf, const ss_sun* sun, double tmax, in
 
 enum class FwdKind { Descent, Uniform };
 
-// default rays per descent strip (each seeded from the previous ray's argmin)
+// rays per descent strip when strips are used by default (each ray seeded from
+// the previous one's argmin)
 constexpr int32_t kDefaultStrip = 10;
-// default ray-rectangle width of the exact descent on grid rays
+// default ray-rectangle width of the descent on grid rays
 constexpr int32_t kDefaultTileW = 256;
 
 ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip,
@@ -189,33 +190,32 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
     a.flags = params->flags;
     const bool light_only = (params->flags & SS_FLAG_LIGHT_ONLY) != 0;
-    // Defaults (measured on GB300: 4096^2 mid workload, polar view): the descent
-    // (exact and light-only) draws grid rays row by row across 256 x 32 ray
-    // rectangles, each seeded from the last finished ray of its column; listed
-    // rays are read as 256 columns of consecutive ids and drawn the same way
-    // (exact mode; light-only listed rays stay unseeded); uniform stepping draws
-    // single rays from row-major runs.
-    const bool strips = kind == FwdKind::Descent;
+    const bool descent = kind == FwdKind::Descent;
+    // Defaults (measured on GB300: 4096^2 mid workload, polar view).  The
+    // descent (exact and light-only) draws grid rays row by row across 256 x 32
+    // ray rectangles, each seeded from the last finished ray of its column
+    // (column seeds); listed rays are read as 256 columns of consecutive ids
+    // and drawn the same way, except in light-only mode where they stay
+    // unseeded (measured faster on the polar view, whose lit rays end at the
+    // root).  Uniform stepping draws single rays from row-major runs.
     int block = params->block_threads ? params->block_threads : 256;
-    const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : (strips ? 32 : 16);
+    const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : (descent ? 32 : 16);
     a.rays_per_block = (int64_t)block * rpt;
-    a.refill_min = params->refill_min > 0 ? params->refill_min : (strips ? 10 : 6);
+    a.refill_min = params->refill_min > 0 ? params->refill_min : (descent ? 10 : 6);
     a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
     a.tile_w = params->ray_tile_w;
-    if (a.tile_w == 0 && strips && rays->mode == SS_RAYS_GRID && a.rays_per_block % kDefaultTileW == 0)
+    if (a.tile_w == 0 && descent && rays->mode == SS_RAYS_GRID &&
+        a.rays_per_block % kDefaultTileW == 0)
         a.tile_w = kDefaultTileW;
     if (a.tile_w > 0 && a.rays_per_block % a.tile_w != 0) return SS_ERR_INVALID_ARG;
-    a.strip = kind == FwdKind::Descent
-                  ? (params->strip_len > 0 ? params->strip_len : (light_only ? 1 : kDefaultStrip))
-                  : 1;
-    // default: single rays with column seeds (no strips); grid rays in rectangles
-    // of at most kColSeedMaxW columns, or runs of ids read as columns
-    // (listed rays in light-only mode stay unseeded: measured faster on the
-    // polar view, whose lit rays end at the root)
-    a.colseed = (strips && params->strip_len == 0 &&
-                 (rays->mode == SS_RAYS_GRID ? (a.tile_w == 0 || a.tile_w <= ss::kColSeedMaxW)
-                                             : !light_only))
+    a.colseed = (descent && params->strip_len == 0 &&
+                 (rays->mode == SS_RAYS_GRID ? a.tile_w <= ss::kColSeedMaxW : !light_only))
                     ? 1 : 0;
+    // strips: explicit strip_len, else (no column seeds) strips of kDefaultStrip,
+    // none in light-only mode
+    a.strip = !descent ? 1
+              : params->strip_len > 0 ? params->strip_len
+              : light_only ? 1 : kDefaultStrip;
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);
