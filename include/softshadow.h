@@ -144,7 +144,13 @@ typedef struct {
                               S in [2, 256]: each lane walks a strip of S
                               neighbouring rays (down a rectangle column, or
                               consecutive ids), seeding from the previous one.
-                              1 = no seeding.  Other calls ignore it.          */
+                              In both seeded modes a ray with no finished
+                              neighbour (a rectangle's first row, a strip's
+                              first ray) is seeded with the best of its
+                              samples j_lo - 1 + 2^k, k = 0, 1, ... and j_hi.
+                              1 = no seeding.  Light-only forward: 0 as
+                              above, any other value = no seeding.  Other
+                              calls ignore it.                                 */
 } ss_params;
 
 /* Ray origins p (Sec. 3.1: view-ray intersection points). */

@@ -129,15 +129,13 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                 }
                 if (r >= 0) {
                     setup_ray<true, kLight>(D.T, grid_rays, L.ray, S.span, rf);
-                    int32_t sj = -1;
-                    float sc = INFINITY;
-                    if (prev_j > 0)
-                        sc = D.poly ? seed_near<true, true, false>(D.T, rf, prev_j, sj)
-                                    : seed_near<true, false, false>(D.T, rf, prev_j, sj);
+                    int32_t sj, n_seed;
+                    const float sc =
+                        D.poly ? seed_ray<true, true, false>(D.T, rf, prev_j, false, sj, n_seed)
+                               : seed_ray<true, false, false>(D.T, rf, prev_j, false, sj, n_seed);
                     if (sj > 0) {
                         walk_begin_seeded<kLight>(w, rf, a.kleaf, sc, sj);
-                        if (kCount) w.nl = min(rf.j_hi, prev_j + kSeedWidth) -
-                                           max(rf.j_lo, prev_j - kSeedWidth) + 1;
+                        if (kCount) w.nl = n_seed;
                     } else {
                         walk_begin<kLight>(w, rf, a.kleaf);
                     }
@@ -159,15 +157,15 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                         L.slot = S.colseed ? r % S.C.w : -1;
                         setup_ray<true, kLight>(D.T, grid_rays, L.ray, S.span, rf);
                         const int32_t pj = S.colseed ? seeds[L.slot] : -1;
-                        int32_t sj = -1;
-                        float sc = INFINITY;
-                        if (pj > 0)
-                            sc = D.poly ? seed_near<true, true, false>(D.T, rf, pj, sj)
-                                        : seed_near<true, false, false>(D.T, rf, pj, sj);
+                        // seeded modes: a ray with no finished neighbour takes sparse samples
+                        const bool geo = !kLight && (S.colseed || a.strip > 1);
+                        int32_t sj, n_seed;
+                        const float sc =
+                            D.poly ? seed_ray<true, true, false>(D.T, rf, pj, geo, sj, n_seed)
+                                   : seed_ray<true, false, false>(D.T, rf, pj, geo, sj, n_seed);
                         if (sj > 0) {
                             walk_begin_seeded<kLight>(w, rf, a.kleaf, sc, sj);
-                            if (kCount) w.nl = min(rf.j_hi, pj + kSeedWidth) -
-                                               max(rf.j_lo, pj - kSeedWidth) + 1;
+                            if (kCount) w.nl = n_seed;
                         } else {
                             walk_begin<kLight>(w, rf, a.kleaf);
                         }

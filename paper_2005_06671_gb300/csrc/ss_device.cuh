@@ -357,6 +357,11 @@ __device__ __forceinline__ bool exit_fast(const Tile& T, double up, double vp, d
     return true;
 }
 
+// 1/rho^2 from 1/(2 rho) (gnomonic setup; recomputed when a parked ray is loaded)
+__device__ __forceinline__ float inv_rho2_of(float inv_2rho) {
+    return __fmul_rn(__fmul_rn(4.0f, inv_2rho), inv_2rho);
+}
+
 // Float32 ray setup for gnomonic tiles.  FP64 only where float32 is not
 // enough: the per-sample slope (a j must be good to ~1e-7 texel at j ~ 10^4)
 // and the usable range; the sun elevation over p and the rise coefficients in
@@ -393,7 +398,7 @@ __device__ __forceinline__ void make_rayf_gnomonic(const Tile& T, double up, dou
     r.b = (float)b;
     r.B = 2.0f * rhof * se;
     r.inv_2rho = 0.5f / rhof;
-    r.inv_rho2 = 4.0f * r.inv_2rho * r.inv_2rho;
+    r.inv_rho2 = inv_rho2_of(r.inv_2rho);
     r.X = kGrid ? 0.0f : (float)(hp - href);
     r.href = (float)href;
     r.tv = se < 0.0f ? -rhof * se : -1.0f;
