@@ -117,10 +117,12 @@ typedef struct {
     int32_t block_threads; /* threads per block, multiple of 32 in [32, 256];
                               0 = 256                                          */
     int32_t leaf_level;    /* forward: subtrees of <= 2^leaf_level samples are
-                              evaluated sample by sample; -1 = default (2)     */
+                              evaluated sample by sample; -1 = default (grid
+                              rays and the batch 1, listed rays 2)             */
     int32_t rays_per_thread; /* forward kernels: a block owns block_threads x
                               rays_per_thread rays, in [0, 4096]; 0 = default
-                              (exact descent 32, otherwise 16)                 */
+                              (descent: grid rays 24, listed rays 32; uniform
+                              stepping 16)                                     */
     int32_t refill_min;    /* forward kernels: a warp's idle lanes take new
                               rays once at least this many are idle, in
                               [0, 32]; 0 = default (exact descent 10, else 6)  */
@@ -151,6 +153,11 @@ typedef struct {
                               1 = no seeding.  Light-only forward: 0 as
                               above, any other value = no seeding.  Other
                               calls ignore it.                                 */
+    int32_t seed_width;    /* seeded descents: a ray seeded from a neighbour's
+                              argmin j evaluates its samples j-w..j+w, w in
+                              [0, 16]; 0 = default (grid rays 1, listed
+                              rays 2: neighbouring view rays can be several
+                              texels apart)                                    */
 } ss_params;
 
 /* Ray origins p (Sec. 3.1: view-ray intersection points). */

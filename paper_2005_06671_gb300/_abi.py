@@ -37,7 +37,8 @@ class SSSun(ctypes.Structure):
 class SSParams(ctypes.Structure):
     _fields_ = [("max_len_m", c_f64), ("step_texels", c_f64), ("flags", c_u32),
                 ("block_threads", c_i32), ("leaf_level", c_i32), ("rays_per_thread", c_i32),
-                ("refill_min", c_i32), ("ray_tile_w", c_i32), ("strip_len", c_i32)]
+                ("refill_min", c_i32), ("ray_tile_w", c_i32), ("strip_len", c_i32),
+                ("seed_width", c_i32)]
 
 
 class SSBatchItem(ctypes.Structure):

@@ -28,11 +28,11 @@ SPACE = {
     "rays_per_thread": (4, 8, 16, 32),
     "ray_tile_w": (0, 16, 32, 64),
     "refill_min": (4, 8, 12),
-    "leaf_level": (2, 3),
+    "leaf_level": (1, 2, 3),
     "strip_len": (0, 1, 6, 10, 16),
 }
 DEFAULT = {"block_threads": 256, "rays_per_thread": 16, "ray_tile_w": 32, "refill_min": 10,
-           "leaf_level": 2, "strip_len": 0}
+           "leaf_level": 1, "strip_len": 0}
 
 
 def default_table_path():

@@ -60,6 +60,7 @@ ss_status check_params(const ss_params* p, double g, int32_t* J, double* delta) 
     if (p->refill_min < 0 || p->refill_min > 32) return SS_ERR_INVALID_ARG;
     if (p->ray_tile_w < 0 || p->ray_tile_w > SS_MAX_DIM) return SS_ERR_INVALID_ARG;
     if (p->strip_len < 0 || p->strip_len > 256) return SS_ERR_INVALID_ARG;
+    if (p->seed_width < 0 || p->seed_width > 16) return SS_ERR_INVALID_ARG;
     double st = p->step_texels == 0.0 ? 0.5 : p->step_texels;
     double d = st * g;
     if (!finite_pos(d)) return SS_ERR_INVALID_ARG;
@@ -187,19 +188,24 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.O.cost = out->cost;
     a.O.counters = (params->flags & SS_FLAG_COUNT_SAMPLES) ? out->counters : nullptr;
     a.stats = mip + L.stats_offset;
-    a.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
+    a.kleaf = params->leaf_level >= 0 ? params->leaf_level : (rays->mode == SS_RAYS_GRID ? 1 : 2);
     a.flags = params->flags;
     const bool light_only = (params->flags & SS_FLAG_LIGHT_ONLY) != 0;
     const bool descent = kind == FwdKind::Descent;
     // Defaults (measured on GB300: 4096^2 mid workload, polar view).  The
-    // descent (exact and light-only) draws grid rays row by row across 256 x 32
+    // descent (exact and light-only) draws grid rays row by row across 256 x 24
     // ray rectangles, each seeded from the last finished ray of its column
-    // (column seeds); listed rays are read as 256 columns of consecutive ids
-    // and drawn the same way, except in light-only mode where they stay
-    // unseeded (measured faster on the polar view, whose lit rays end at the
-    // root).  Uniform stepping draws single rays from row-major runs.
+    // (column seeds, window +-1, leaf level 1); listed rays are read as 256
+    // columns of consecutive ids and drawn the same way (window +-2: adjacent
+    // view rays can be several texels apart; leaf level 2), except in
+    // light-only mode where they stay unseeded (measured faster on the polar
+    // view, whose lit rays end at the root).  Uniform stepping draws single
+    // rays from row-major runs.
     int block = params->block_threads ? params->block_threads : 256;
-    const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : (descent ? 32 : 16);
+    const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread
+                        : !descent                     ? 16
+                        : rays->mode == SS_RAYS_GRID   ? 24
+                                                       : 32;
     a.rays_per_block = (int64_t)block * rpt;
     a.refill_min = params->refill_min > 0 ? params->refill_min : (descent ? 10 : 6);
     a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
@@ -216,6 +222,7 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.strip = !descent ? 1
               : params->strip_len > 0 ? params->strip_len
               : light_only ? 1 : kDefaultStrip;
+    a.seed_w = params->seed_width > 0 ? params->seed_width : (rays->mode == SS_RAYS_GRID ? 1 : 2);
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);
@@ -292,12 +299,13 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
     B.args.total_chunks = prefix[n];
     B.args.n_items = n;
     B.args.chunk_rays = chunk;
-    B.args.kleaf = params->leaf_level < 0 ? 2 : params->leaf_level;
+    B.args.kleaf = params->leaf_level < 0 ? 1 : params->leaf_level;   // grid rays
     B.args.refill_min = params->refill_min > 0 ? params->refill_min : 6;
     B.args.light_only = (params->flags & SS_FLAG_LIGHT_ONLY) ? 1 : 0;
     B.args.strip = params->strip_len > 0 ? params->strip_len
                                          : (B.args.light_only ? 1 : kDefaultStrip);
     B.args.colseed = (params->strip_len == 0 && !B.args.light_only && tile_w > 0) ? 1 : 0;
+    B.args.seed_w = params->seed_width > 0 ? params->seed_width : 1;   // grid rays
     return SS_OK;
 }
 

@@ -75,17 +75,20 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
     BatchItemDesc& D = reinterpret_cast<BatchItemDesc*>(smem)[wid];
     WarpSched& S = reinterpret_cast<WarpSched*>(
         smem + (size_t)(blockDim.x >> 5) * sizeof(BatchItemDesc))[wid];
-    // column seeds of this warp's chunk: argmin of the last finished ray per column
+    // column seeds of this warp's chunk: argmin of the last finished ray per
+    // column, and that ray's origin
     int32_t* seeds = reinterpret_cast<int32_t*>(
         smem + (size_t)(blockDim.x >> 5) * (sizeof(BatchItemDesc) + sizeof(WarpSched))) +
-        wid * kBatchSeedW;
+        wid * 3 * kBatchSeedW;
+    float* seed_u = reinterpret_cast<float*>(seeds + kBatchSeedW);
+    float* seed_v = seed_u + kBatchSeedW;
     // Each lane's ray as an id within the instance, and its seed column: a warp
     // moves to its next chunk (same instance) while other lanes still walk rays
     // of the previous one, so a lane's ray must not be kept as an index into
     // the warp's current chunk.
     LaneRay& L = reinterpret_cast<LaneRay*>(
         smem + (size_t)(blockDim.x >> 5) *
-                   (sizeof(BatchItemDesc) + sizeof(WarpSched) + kBatchSeedW * sizeof(int32_t)))
+                   (sizeof(BatchItemDesc) + sizeof(WarpSched) + 3 * kBatchSeedW * sizeof(int32_t)))
         [threadIdx.x];
     const Rays grid_rays = { 0, 0, nullptr, nullptr };
     if (lane == 0) {
@@ -116,9 +119,14 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
             // to the next one, seeded from this ray's argmin (same instance)
             if (done) {
                 finish_ray(D.T, grid_rays, D.O, L.ray, w.best, w.bestj, w.nb, w.nl);
-                if (L.slot >= 0 && w.bestj > 0) seeds[L.slot] = w.bestj;
+                if (L.slot >= 0 && w.bestj > 0) {
+                    seeds[L.slot] = w.bestj;
+                    seed_u[L.slot] = rf.u0;
+                    seed_v[L.slot] = rf.v0;
+                }
                 done = false;
                 int32_t prev_j = -1;
+                const float su = rf.u0, sv = rf.v0;
                 if (left > 0) {          // next ray of the strip: a row down, or the next id
                     prev_j = w.bestj;
                     L.ray += D.tile_w > 0 ? (int64_t)D.T.nx : 1;
@@ -129,10 +137,12 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                 }
                 if (r >= 0) {
                     setup_ray<true, kLight>(D.T, grid_rays, L.ray, S.span, rf);
+                    const bool near = prev_j > 0;
+                    const int32_t jc = near ? seed_centre(rf, prev_j, su - rf.u0, sv - rf.v0) : -1;
                     int32_t sj, n_seed;
                     const float sc =
-                        D.poly ? seed_ray<true, true, false>(D.T, rf, prev_j, false, sj, n_seed)
-                               : seed_ray<true, false, false>(D.T, rf, prev_j, false, sj, n_seed);
+                        D.poly ? seed_ray<true, true, false>(D.T, rf, near, jc, a.seed_w, false, sj, n_seed)
+                               : seed_ray<true, false, false>(D.T, rf, near, jc, a.seed_w, false, sj, n_seed);
                     if (sj > 0) {
                         walk_begin_seeded<kLight>(w, rf, a.kleaf, sc, sj);
                         if (kCount) w.nl = n_seed;
@@ -157,12 +167,16 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                         L.slot = S.colseed ? r % S.C.w : -1;
                         setup_ray<true, kLight>(D.T, grid_rays, L.ray, S.span, rf);
                         const int32_t pj = S.colseed ? seeds[L.slot] : -1;
+                        const bool near = pj > 0;
+                        const int32_t jc =
+                            near ? seed_centre(rf, pj, seed_u[L.slot] - rf.u0, seed_v[L.slot] - rf.v0)
+                                 : -1;
                         // seeded modes: a ray with no finished neighbour takes sparse samples
                         const bool geo = !kLight && (S.colseed || a.strip > 1);
                         int32_t sj, n_seed;
                         const float sc =
-                            D.poly ? seed_ray<true, true, false>(D.T, rf, pj, geo, sj, n_seed)
-                                   : seed_ray<true, false, false>(D.T, rf, pj, geo, sj, n_seed);
+                            D.poly ? seed_ray<true, true, false>(D.T, rf, near, jc, a.seed_w, geo, sj, n_seed)
+                                   : seed_ray<true, false, false>(D.T, rf, near, jc, a.seed_w, geo, sj, n_seed);
                         if (sj > 0) {
                             walk_begin_seeded<kLight>(w, rf, a.kleaf, sc, sj);
                             if (kCount) w.nl = n_seed;
@@ -214,7 +228,10 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                     S.n_strips = strip_count(S.C, S.colseed ? 1 : a.strip);
                     S.c_next = 0;
                 }
-                for (int i = lane; i < kBatchSeedW; i += 32) seeds[i] = -1;
+                for (int i = lane; i < kBatchSeedW; i += 32) {
+                    seeds[i] = -1;
+                    seed_u[i] = seed_v[i] = 0.0f;
+                }
                 __syncwarp();
             }
             act = __ballot_sync(kFull, r >= 0 && !done);
@@ -260,7 +277,7 @@ void batch_layout(void* ws, int32_t n_items, unsigned long long** counter, Batch
 
 cudaError_t launch_batch_forward(const BatchArgs& a, int block, bool count, cudaStream_t s) {
     const size_t smem = (size_t)(block / 32) *
-                            (sizeof(BatchItemDesc) + sizeof(WarpSched) + kBatchSeedW * sizeof(int32_t)) +
+                            (sizeof(BatchItemDesc) + sizeof(WarpSched) + 3 * kBatchSeedW * sizeof(int32_t)) +
                         (size_t)block * sizeof(LaneRay);
     if (count) {
         if (a.light_only)

@@ -35,6 +35,7 @@ struct BatchArgs {
     int32_t light_only;             // SS_FLAG_LIGHT_ONLY
     int32_t strip;                  // rays per seeded strip (1 = no seeding)
     int32_t colseed;                // rectangular chunks: single rays, column seeds
+    int32_t seed_w;                 // half-width of a seed window
 };
 
 constexpr int32_t kBatchSeedW = 64;    // widest chunk with a column-seed table

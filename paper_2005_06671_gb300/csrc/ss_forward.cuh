@@ -70,18 +70,20 @@ __device__ __forceinline__ int32_t draw_strip(int32_t n_strips, int32_t* s_next,
 // Exact walks (light-only walks: dp_light_kernel below).
 // Column seeds (grid rays in rectangles of at most kColSeedMaxW columns, the
 // default): lanes draw single rays row by row across the block's rectangle and
-// each ray starts from the lowest of its own samples near the argmin of the
-// last finished ray of its column (a shared-memory table), typically one or two
-// rows above.  Single-ray draws keep the block's tail to one ray per lane.
+// each ray starts from the lowest of its own samples within +-seed_w of where
+// the argmin of the last finished ray of its column (a shared-memory table of
+// argmin and origin, typically one or two rows above) lies along this ray
+// (seed_centre).  Single-ray draws keep the block's tail to one ray per lane;
+// a ray drawn before any ray of its column has finished takes the sparse
+// samples of seed_geo instead.
 //
 // Strips: the block's rays are cut into strips of a.strip neighbouring rays
 // (down a column of the block's rectangle for rectangular grid chunks, else
-// consecutive ids).  A lane walks its strip's rays in order; each ray after
-// the first starts its descent with best = the lowest of its own samples
-// within +-kSeedWidth of the previous ray's argmin.  Neighbouring rays are
-// parallel and one texel apart, so their minima sit at nearly the same sample
-// and the walk prunes from the start (a seed is a sample cost, an upper bound
-// of the minimum, so the result is unchanged).
+// consecutive ids).  A lane walks its strip's rays in order, each seeded from
+// the previous ray's argmin, the first from sparse samples.  Neighbouring rays
+// are parallel and one texel apart, so their minima sit at nearly the same
+// terrain point and the walk prunes from the start (a seed is a sample cost,
+// an upper bound of the minimum, so the result is unchanged).
 // Each loop iteration is one probe of the exact descent (walk_step) per
 // walking lane.  Lanes whose ray is done wait until refill_min of them are
 // (or all are); the warp then writes their results and sets up their next
@@ -95,15 +97,19 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
         s_lev.pitch[threadIdx.x] = (uint32_t)a.P.pitch[threadIdx.x];
     }
     __shared__ int32_t s_seed[kColSeedMaxW];   // column seeds: argmin of a finished ray
+    __shared__ float s_su[kColSeedMaxW], s_sv[kColSeedMaxW];   // and that ray's origin
     const ChunkRange P = block_pool(a, &s_next);
     // Column seeds.  Grid rectangles: columns of the rectangle.  Runs of ids
     // (listed rays): the run is read as LW columns of LH consecutive ids each,
     // drawn row by row, so an id is drawn a round after the id before it.
     const bool colseed = a.colseed != 0;
-    const int32_t LW = (colseed && !P.rect) ? min(kColSeedMaxW / 4, P.cnt) : 0;
+    const int32_t LW = (colseed && !P.rect) ? min(kListSeedCols, P.cnt) : 0;
     const int32_t LH = LW > 0 ? (P.cnt + LW - 1) / LW : 0;
     if (colseed)
-        for (int i = threadIdx.x; i < (P.rect ? P.w : LW); i += blockDim.x) s_seed[i] = -1;
+        for (int i = threadIdx.x; i < (P.rect ? P.w : LW); i += blockDim.x) {
+            s_seed[i] = -1;
+            s_su[i] = s_sv[i] = 0.0f;
+        }
     __syncthreads();
     const float span = a.stats[0] - a.stats[1];
     const int32_t kleaf = a.kleaf, levels = a.P.levels;
@@ -123,14 +129,24 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
         const unsigned want = __ballot_sync(kFull, (r < 0 || done) && (left > 0 || open));
         if (act == 0 || __popc(want) >= a.refill_min) {
             bool fresh = false;
-            int32_t prev_j = -1;     // argmin of the strip's previous ray
+            int32_t prev_j = -1;     // a neighbour's argmin, and its origin:
+            float su = 0.0f, sv = 0.0f;
             if (done) {
                 finish_ray<kStereo, true>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
                                     w.nb, w.nl);
-                if (colseed && w.bestj > 0) s_seed[P.rect ? r % P.w : r / LH] = w.bestj;
+                if (colseed && w.bestj > 0) {
+                    const int32_t c = P.rect ? r % P.w : r / LH;
+                    s_seed[c] = w.bestj;
+                    if (kGrid) {
+                        s_su[c] = rf.u0;
+                        s_sv[c] = rf.v0;
+                    }
+                }
                 done = false;
                 if (left > 0) {
                     prev_j = w.bestj;
+                    su = rf.u0;
+                    sv = rf.v0;
                     r += stride;
                     --left;
                     fresh = true;
@@ -148,22 +164,32 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
                             left = 0;
                             fresh = true;
                             prev_j = s_seed[ns % LW];
+                            su = s_su[ns % LW];
+                            sv = s_sv[ns % LW];
                         }
                     } else {
                         const Strip st = strip_of(P, S, ns);
                         r = st.first;
                         left = st.count - 1;
                         fresh = true;
-                        if (colseed) prev_j = s_seed[r % P.w];   // a ray above in this column
+                        if (colseed) {                   // a ray above in this column
+                            prev_j = s_seed[r % P.w];
+                            su = s_su[r % P.w];
+                            sv = s_sv[r % P.w];
+                        }
                     }
                 }
             }
             if (fresh) {
                 setup_ray<kGrid, false, kStereo>(a.T, a.R, chunk_ray(P, a.T.nx, r), span, rf);
+                const bool near = prev_j > 0;
+                const int32_t jc = !near ? -1
+                                   : kGrid ? seed_centre(rf, prev_j, su - rf.u0, sv - rf.v0)
+                                           : prev_j;
                 int32_t sj, n_seed;
                 // seeded modes: a ray with no finished neighbour takes sparse samples
-                const float sc = seed_ray<kGrid, kPoly, kStereo>(a.T, rf, prev_j, colseed || S > 1,
-                                                                 sj, n_seed);
+                const float sc = seed_ray<kGrid, kPoly, kStereo>(a.T, rf, near, jc, a.seed_w,
+                                                                 colseed || S > 1, sj, n_seed);
                 if (sj > 0) {
                     walk_begin_seeded<false>(w, rf, kleaf, sc, sj);
                     if (kCount) w.nl = n_seed;
@@ -218,6 +244,7 @@ dp_light_kernel(const __grid_constant__ FwdArgs a) {
     __shared__ LevelTab s_lev;
     __shared__ int32_t s_next;
     __shared__ int32_t s_seed[kColSeedMaxW];   // column seeds: argmin of a finished ray
+    __shared__ float s_su[kColSeedMaxW], s_sv[kColSeedMaxW];   // and that ray's origin
     __shared__ uint32_t s_q[8][kWr + 1][kQSlots];
     if (threadIdx.x < kMaxLevels) {
         s_lev.ptr[threadIdx.x] = a.P.ptr[threadIdx.x];
@@ -228,11 +255,14 @@ dp_light_kernel(const __grid_constant__ FwdArgs a) {
     // finished ray of its column of the rectangle).  Runs of ids (listed rays
     // with column seeds): LW columns of LH consecutive ids each, row by row.
     const bool colseed = a.colseed != 0;
-    const int32_t LW = (colseed && !P.rect) ? min(kColSeedMaxW / 4, P.cnt) : 0;
+    const int32_t LW = (colseed && !P.rect) ? min(kListSeedCols, P.cnt) : 0;
     const int32_t LH = LW > 0 ? (P.cnt + LW - 1) / LW : 0;
     const int32_t n_order = LW > 0 ? LW * LH : P.cnt;
     if (colseed)
-        for (int i = threadIdx.x; i < (P.rect ? P.w : LW); i += blockDim.x) s_seed[i] = -1;
+        for (int i = threadIdx.x; i < (P.rect ? P.w : LW); i += blockDim.x) {
+            s_seed[i] = -1;
+            s_su[i] = s_sv[i] = 0.0f;
+        }
     __syncthreads();
     const float span = a.stats[0] - a.stats[1];
     const int32_t kleaf = a.kleaf, levels = a.P.levels;
@@ -253,7 +283,14 @@ dp_light_kernel(const __grid_constant__ FwdArgs a) {
             if (done) {
                 finish_ray<kStereo, true>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
                                           w.nb, w.nl);
-                if (colseed && w.bestj > 0) s_seed[P.rect ? r % P.w : r / LH] = w.bestj;
+                if (colseed && w.bestj > 0) {
+                    const int32_t c = P.rect ? r % P.w : r / LH;
+                    s_seed[c] = w.bestj;
+                    if (kGrid) {
+                        s_su[c] = rf.u0;
+                        s_sv[c] = rf.v0;
+                    }
+                }
                 done = false;
                 r = -1;
             }
@@ -285,14 +322,18 @@ dp_light_kernel(const __grid_constant__ FwdArgs a) {
                 r = (int32_t)q[kWr][slot];
                 if (r >= 0) {
                     Pack::load(q, slot, rf);
-                    const int32_t prev_j = colseed ? s_seed[P.rect ? r % P.w : r / LH] : -1;
-                    int32_t sj = -1;
-                    float sc = INFINITY;
-                    if (prev_j > 0) sc = seed_near<kGrid, kPoly, kStereo>(a.T, rf, prev_j, sj);
+                    const int32_t c = P.rect ? r % P.w : r / LH;
+                    const int32_t prev_j = colseed ? s_seed[c] : -1;
+                    const bool near = prev_j > 0;
+                    const int32_t jc = !near ? -1
+                                       : kGrid ? seed_centre(rf, prev_j, s_su[c] - rf.u0, s_sv[c] - rf.v0)
+                                               : prev_j;
+                    int32_t sj, n_seed;
+                    const float sc = seed_ray<kGrid, kPoly, kStereo>(a.T, rf, near, jc, a.seed_w,
+                                                                     false, sj, n_seed);
                     if (sj > 0) {
                         walk_begin_seeded<true>(w, rf, kleaf, sc, sj);
-                        if (kCount) w.nl = min(rf.j_hi, prev_j + kSeedWidth) -
-                                           max(rf.j_lo, prev_j - kSeedWidth) + 1;
+                        if (kCount) w.nl = n_seed;
                     } else {
                         walk_begin<true>(w, rf, kleaf);
                     }

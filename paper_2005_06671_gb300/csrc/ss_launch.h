@@ -35,9 +35,11 @@ struct FwdArgs {
     int32_t tile_w;           // grid mode: ray-rectangle width (0 = row-major runs)
     int32_t strip;            // descent: rays per strip (1 = no seeding)
     int32_t colseed;          // descent, grid rays in rectangles: column seeds
+    int32_t seed_w;           // descent: half-width of a seed window
 };
 
-constexpr int32_t kColSeedMaxW = 1024;   // widest rectangle with a column-seed table
+constexpr int32_t kColSeedMaxW = 512;    // widest rectangle with a column-seed table
+constexpr int32_t kListSeedCols = 256;   // listed rays: columns of consecutive ids
 
 struct BwdArgs {
     Tile T;

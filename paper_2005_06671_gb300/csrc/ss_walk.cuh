@@ -310,16 +310,14 @@ __device__ __forceinline__ void walk_begin_seeded(Walk& w, const RayF& rf, int32
     w.bestj = use ? seed_j : -1;
 }
 
-// Best of the ray's own samples within +-kSeedWidth of index j0 (clipped to
+// Best of the ray's own samples within +-sw of index j0 (clipped to
 // [j_lo, j_hi]); j_out = -1 when none is usable.  Smallest index on ties.
-constexpr int32_t kSeedWidth = 2;
-
 template <bool kGrid, bool kPoly, bool kStereo>
-__device__ __forceinline__ float seed_near(const Tile& T, const RayF& rf, int32_t j0,
+__device__ __forceinline__ float seed_near(const Tile& T, const RayF& rf, int32_t j0, int32_t sw,
                                            int32_t& j_out) {
     float best = INFINITY;
     j_out = -1;
-    const int32_t lo = max(rf.j_lo, j0 - kSeedWidth), hi = min(rf.j_hi, j0 + kSeedWidth);
+    const int32_t lo = max(rf.j_lo, j0 - sw), hi = min(rf.j_hi, j0 + sw);
     for (int32_t j = lo; j <= hi; ++j) {
         float rise;
         const float c = leaf_cost<kGrid, kPoly, kStereo>(T, rf, j, rise);
@@ -358,20 +356,40 @@ __device__ __forceinline__ float seed_geo(const Tile& T, const RayF& rf, int32_t
     return best;
 }
 
-// Seed of a newly drawn ray: near the argmin prev_j of a neighbouring ray
-// (prev_j > 0), else the sparse samples of seed_geo when `geo`, else none
-// (j_out = -1).  n_out: samples evaluated (the probe counters include them).
+// Where this ray meets the terrain point of a parallel neighbouring ray's
+// argmin j_src: p + j a = p_src + j_src a gives j = j_src + d.a / |a|^2,
+// d = p_src - p (texels), a the per-sample step of this ray at its origin.
+// A neighbour one row up along a ray running down the columns is two samples
+// ahead (0.5-texel steps), so a window around j_src alone would miss it.
+// (Grid rays.  Listed rays keep the window at j_src: on the polar view the
+// centring saved 5% of the probes but measured 4% slower.)
+__device__ __forceinline__ int32_t seed_centre(const RayF& rf, int32_t j_src, float du, float dv) {
+    const float a2 = rf.au * rf.au + rf.av * rf.av;
+    const float sh = a2 > 0.0f ? __fdividef(du * rf.au + dv * rf.av, a2) : 0.0f;
+    return j_src + (int32_t)rintf(fminf(fmaxf(sh, -1.0e6f), 1.0e6f));
+}
+
+// Seed of a newly drawn ray: with a finished neighbour (`near`), its samples
+// within +-sw of jc (seed_centre of the neighbour's argmin); else, or when
+// that window holds no usable sample, the sparse samples of seed_geo when
+// `geo`; else none (j_out = -1).  n_out: samples evaluated (the probe counters
+// include them).
 template <bool kGrid, bool kPoly, bool kStereo>
-__device__ __forceinline__ float seed_ray(const Tile& T, const RayF& rf, int32_t prev_j, bool geo,
-                                          int32_t& j_out, int32_t& n_out) {
-    if (prev_j > 0) {
-        n_out = max(0, min(rf.j_hi, prev_j + kSeedWidth) - max(rf.j_lo, prev_j - kSeedWidth) + 1);
-        return seed_near<kGrid, kPoly, kStereo>(T, rf, prev_j, j_out);
-    }
-    if (geo) return seed_geo<kGrid, kPoly, kStereo>(T, rf, j_out, n_out);
+__device__ __forceinline__ float seed_ray(const Tile& T, const RayF& rf, bool near, int32_t jc,
+                                          int32_t sw, bool geo, int32_t& j_out, int32_t& n_out) {
+    float best = INFINITY;
     j_out = -1;
     n_out = 0;
-    return INFINITY;
+    if (near) {
+        n_out = max(0, min(rf.j_hi, jc + sw) - max(rf.j_lo, jc - sw) + 1);
+        best = seed_near<kGrid, kPoly, kStereo>(T, rf, jc, sw, j_out);
+    }
+    if (j_out < 0 && geo) {
+        int32_t n_geo;
+        best = seed_geo<kGrid, kPoly, kStereo>(T, rf, j_out, n_geo);
+        n_out += n_geo;
+    }
+    return best;
 }
 
 // One probe of the exact descent and the state update; true when finished.

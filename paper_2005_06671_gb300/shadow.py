@@ -106,10 +106,10 @@ def ss_build_maxmip(hf: Heightfield, mip=None, stream=None):
 
 # ----------------------------------------------------------------- forward
 def _params(max_len_m, step_texels, flags, block_threads, leaf_level, rays_per_thread=0,
-            refill_min=0, ray_tile_w=0, strip_len=0):
+            refill_min=0, ray_tile_w=0, strip_len=0, seed_width=0):
     return SSParams(float(max_len_m), float(step_texels), int(flags), int(block_threads),
                     int(leaf_level), int(rays_per_thread), int(refill_min), int(ray_tile_w),
-                    int(strip_len))
+                    int(strip_len), int(seed_width))
 
 
 def _rays(hf, uv, lift):
@@ -146,12 +146,12 @@ def _outputs(n, device, want_cost, count, out):
 
 def _forward(fn_name, hf, mip, sun, max_len_m, step_texels, uv, lift, flags, block_threads,
              leaf_level, want_cost, out, stream, rays_per_thread=0, refill_min=0, ray_tile_w=0,
-             strip_len=0):
+             strip_len=0, seed_width=0):
     rays, n = _rays(hf, uv, lift)
     count = bool(flags & SS_FLAG_COUNT_SAMPLES)
     oc, res = _outputs(n, hf.h.device, want_cost, count, out)
     prm = _params(max_len_m, step_texels, flags, block_threads, leaf_level, rays_per_thread,
-                  refill_min, ray_tile_w, strip_len)
+                  refill_min, ray_tile_w, strip_len, seed_width)
     fn = getattr(_abi.lib(), fn_name)
     check(fn(ctypes.byref(hf.c()), _ptr(mip), ctypes.byref(rays), ctypes.byref(sun.c()),
              ctypes.byref(prm), ctypes.byref(oc), _stream_ptr(stream)), fn_name)
@@ -161,14 +161,15 @@ def _forward(fn_name, hf, mip, sun, max_len_m, step_texels, uv, lift, flags, blo
 def ss_shadow_forward(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
                       lift=None, count_samples=False, block_threads=0, leaf_level=-1,
                       want_cost=True, out=None, stream=None, rays_per_thread=0, refill_min=0,
-                      ray_tile_w=0, light_only=False, strip_len=0):
+                      ray_tile_w=0, light_only=False, strip_len=0, seed_width=0):
     """Exact max-mip descent.  Returns dict(light, argmin, cost, counters).
     light_only: saturation cutoffs (exact light; argmin/cost exact in the penumbra).
-    strip_len: rays per seeded strip (0 = default, 1 = no seeding)."""
+    strip_len: rays per seeded strip (0 = default, 1 = no seeding).
+    seed_width: half-width of a seed window (0 = default)."""
     flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (SS_FLAG_LIGHT_ONLY if light_only else 0)
     return _forward("ss_shadow_forward", hf, mip, sun, max_len_m, step_texels, uv, lift, flags,
                     block_threads, leaf_level, want_cost, out, stream, rays_per_thread,
-                    refill_min, ray_tile_w, strip_len)
+                    refill_min, ray_tile_w, strip_len, seed_width)
 
 
 def ss_shadow_uniform(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
@@ -258,7 +259,7 @@ class Batch:
 
     def __init__(self, hfs, suns, max_len_m, step_texels=0.5, count_samples=False,
                  want_cost=False, block_threads=0, leaf_level=-1, rays_per_thread=0,
-                 refill_min=0, ray_tile_w=0, light_only=False, strip_len=0):
+                 refill_min=0, ray_tile_w=0, light_only=False, strip_len=0, seed_width=0):
         if len(hfs) != len(suns) or not hfs:
             raise ValueError("need one sun per heightfield, at least one item")
         self.hfs, self.suns = list(hfs), list(suns)
@@ -266,7 +267,7 @@ class Batch:
         flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (SS_FLAG_LIGHT_ONLY if light_only else 0)
         self.params = SSParams(float(max_len_m), float(step_texels), int(flags), int(block_threads),
                                int(leaf_level), int(rays_per_thread), int(refill_min),
-                               int(ray_tile_w), int(strip_len))
+                               int(ray_tile_w), int(strip_len), int(seed_width))
         n = len(hfs)
         self.items = (_abi.SSBatchItem * n)()
         self.mips, self.outs = [], []

@@ -76,6 +76,8 @@ def _fwd(hf, sun, prm, rays, out, mip=FAKE):
     (lambda a: setattr(a[2], "leaf_level", 40), 1),
     (lambda a: setattr(a[2], "strip_len", -1), 1),
     (lambda a: setattr(a[2], "strip_len", 257), 1),
+    (lambda a: setattr(a[2], "seed_width", -1), 1),
+    (lambda a: setattr(a[2], "seed_width", 17), 1),
     (lambda a: setattr(a[2], "rays_per_thread", -1), 1),
     (lambda a: setattr(a[2], "rays_per_thread", 5000), 1),
     (lambda a: setattr(a[2], "refill_min", 33), 1),

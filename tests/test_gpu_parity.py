@@ -123,13 +123,17 @@ def test_descent_tuning_knobs_do_not_change_results(leaf_level, block):
     assert np.array_equal(out["cost"].view(np.uint32), ref["cost"].view(np.uint32))
 
 
-@pytest.mark.parametrize("strip,tile_w,rpt", [(0, 0, 0), (0, 32, 3), (0, 0, 7), (1, 0, 0),
-                                               (3, 0, 0), (10, 32, 32), (33, 16, 8),
-                                               (10, 64, 1), (256, 32, 64), (7, 0, 5)])
-def test_seeded_strips_do_not_change_results(strip, tile_w, rpt):
+@pytest.mark.parametrize("strip,tile_w,rpt,sw", [(0, 0, 0, 0), (0, 32, 3, 0), (0, 0, 7, 0),
+                                                  (1, 0, 0, 0), (3, 0, 0, 0), (10, 32, 32, 0),
+                                                  (33, 16, 8, 0), (10, 64, 1, 0),
+                                                  (256, 32, 64, 0), (7, 0, 5, 0), (0, 0, 0, 1),
+                                                  (0, 0, 0, 16), (4, 0, 0, 5)])
+def test_seeded_strips_do_not_change_results(strip, tile_w, rpt, sw):
     """Seeded walks (column seeds by default, strip_len 0; strips of S rays;
-    none) in grid and list mode, strips longer than a rectangle column, odd
-    and partial chunks: the same argmin and cost bits as uniform stepping."""
+    none; seed windows of several widths; sparse-sample seeds for rays with
+    no finished neighbour) in grid and list mode, strips longer than a
+    rectangle column, odd and partial chunks: the same argmin and cost bits as
+    uniform stepping."""
     inst = make_instance("diff", n=320)
     h, g = inst["h"], inst["g"]
     elev, az = inst["suns"][1]
@@ -138,13 +142,13 @@ def test_seeded_strips_do_not_change_results(strip, tile_w, rpt):
     hf = ss.Heightfield(_dev(h), g, R)
     mip = ss.ss_build_maxmip(hf)
     res = ss.ss_shadow_forward(hf, mip, ss.Sun(*sun), inst["lmax"], strip_len=strip,
-                               ray_tile_w=tile_w, rays_per_thread=rpt)
+                               ray_tile_w=tile_w, rays_per_thread=rpt, seed_width=sw)
     assert np.array_equal(res["argmin"].cpu().numpy(), ref["argmin"])
     assert np.array_equal(res["cost"].cpu().numpy().view(np.uint32), ref["cost"].view(np.uint32))
     uv = random_origins(5000, 320, 320, seed=strip)
     uv = uv[np.argsort(uv[:, 1] * 400 + uv[:, 0])]          # neighbours next to each other
     a = ss.ss_shadow_forward(hf, mip, ss.Sun(*sun), inst["lmax"], uv=_dev(uv), strip_len=strip,
-                             rays_per_thread=rpt)
+                             rays_per_thread=rpt, seed_width=sw)
     b = ss.ss_shadow_uniform(hf, mip, ss.Sun(*sun), inst["lmax"], uv=_dev(uv))
     assert torch.equal(a["argmin"], b["argmin"])
     assert torch.equal(a["cost"].view(torch.int32), b["cost"].view(torch.int32))
