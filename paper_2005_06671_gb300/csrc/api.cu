@@ -120,6 +120,22 @@ ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, doubl
     T.sy_f = (float)s[1];
     T.R_f = (float)hf->radius_m;
     T.alpha_f = (float)sun->angular_radius_rad;
+    auto split = [](double x, float& hi, float& lo) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+    };
+    const double g = hf->texel_m, R = hf->radius_m;
+    split(g, T.g_hi, T.g_lo);
+    float r_hi;
+    split(R, r_hi, T.R_lo);
+    split(R * R, T.RR_hi, T.RR_lo);
+    split(delta, T.delta_hi, T.delta_lo);
+    split(T.inv_gR, T.igR_hi, T.igR_lo);
+    split(R * s[0], T.Rsx_hi, T.Rsx_lo);
+    split(R * s[1], T.Rsy_hi, T.Rsy_lo);
+    float sz_hi;
+    split(s[2], sz_hi, T.sz_lo);
+    T.szR_f = (float)(s[2] / R);
     return T;
 }
 

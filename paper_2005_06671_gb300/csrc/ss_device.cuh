@@ -52,6 +52,9 @@ struct Tile {
     float sz_f;                // (float)sz
     float alpha_f;
     float sx_f, sy_f, R_f;     // (float)sx, (float)sy, (float)R
+    // float-float (hi + lo) copies for the grid-ray setup (df_* below)
+    float g_hi, g_lo, R_lo, RR_hi, RR_lo, delta_hi, delta_lo, igR_hi, igR_lo;
+    float Rsx_hi, Rsx_lo, Rsy_hi, Rsy_lo, sz_lo, szR_f;
 };
 
 struct Rays {
@@ -143,13 +146,21 @@ __device__ __forceinline__ void set_gconst(const Tile& T, RayF& r) {
     r.gconst = kGuardRel * (r.guard0 + 2.0f * rmax);
 }
 
+// Texel of grid ray r: r < nx ny <= 2^32 (the host checks pitch ny <= 2^32),
+// so a 32-bit unsigned division is exact.
+__device__ __forceinline__ void grid_uv(const Tile& T, int64_t r, int32_t& u, int32_t& v) {
+    const uint32_t rr = (uint32_t)r, q = rr / (uint32_t)T.nx;
+    v = (int32_t)q;
+    u = (int32_t)(rr - q * (uint32_t)T.nx);
+}
+
 // Origin height (FP64) of ray r.
 __device__ __forceinline__ void ray_origin(const Tile& T, const Rays& R, int64_t r,
                                            double& up, double& vp, double& hp, double& href,
                                            int32_t& oi0, int32_t& oj0, double ow[4]) {
     if (R.mode == 0) {
-        int64_t v = r / T.nx;
-        int64_t u = r - v * T.nx;
+        int32_t u, v;
+        grid_uv(T, r, u, v);
         up = (double)u;
         vp = (double)v;
         float hv = T.h[v * T.pitch + u];
@@ -357,9 +368,179 @@ __device__ __forceinline__ bool exit_fast(const Tile& T, double up, double vp, d
     return true;
 }
 
+// ------------------------------------------------------- float-float (df)
+// A value carried as an unevaluated sum hi + lo of two floats (about 48
+// significant bits), built from the error-free transformations of Dekker and
+// Knuth: TwoSum, and TwoProd through the fused multiply-add.  Every operation
+// below is an explicitly rounded intrinsic, so the compiler can neither
+// contract nor reorder it (that would break the error-free steps).  Relative
+// error of add/mul ~2^-44; used where the grid-ray setup needs more than
+// float32 (the per-sample slope) without the GB300's slow FP64 pipe.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{ s, e };
+}
+
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return DF{ s, __fsub_rn(b, __fsub_rn(s, a)) };
+}
+
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    const DF s = df_two_sum(x.hi, y.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ DF df_neg(DF x) { return DF{ -x.hi, -x.lo }; }
+
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+    return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_mul_f(DF x, float y) {
+    const float p = __fmul_rn(x.hi, y);
+    const float e = __fmaf_rn(x.lo, y, __fmaf_rn(x.hi, y, -p));
+    return df_fast_two_sum(p, e);
+}
+
+// sqrt(x), x > 0: float seed and one Newton correction, r + (x - r^2) / (2 r)
+__device__ __forceinline__ DF df_sqrt(DF x) {
+    const float r = __fsqrt_rn(x.hi);
+    const float p = __fmul_rn(r, r);
+    const float pe = __fmaf_rn(r, r, -p);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
+    return df_fast_two_sum(r, __fdiv_rn(res, __fmul_rn(2.0f, r)));
+}
+
+// x / y: float quotient and one correction, q + (x - q y) / y
+__device__ __forceinline__ DF df_div(DF x, DF y) {
+    const float q = __fdiv_rn(x.hi, y.hi);
+    const DF qy = df_mul_f(y, q);
+    const DF rem = df_add(x, df_neg(qy));
+    return df_fast_two_sum(q, __fdiv_rn(rem.hi, y.hi));
+}
+
+__device__ __forceinline__ double df_to_double(DF x) { return (double)x.hi + (double)x.lo; }
+
 // 1/rho^2 from 1/(2 rho) (gnomonic setup; recomputed when a parked ray is loaded)
 __device__ __forceinline__ float inv_rho2_of(float inv_2rho) {
     return __fmul_rn(__fmul_rn(4.0f, inv_2rho), inv_2rho);
+}
+
+// exit_fast for a grid ray (origin (u, v) inside the tile) with float-float
+// slope and projective coefficient: the same float estimate, and the same
+// exact FP64 test (from the float-float values) when the estimate is in doubt.
+__device__ __forceinline__ bool exit_fast_df(const Tile& T, float u, float v, DF Au, DF Av, DF b,
+                                             int32_t& j_hi) {
+    if (!(1.0f + b.hi * (float)T.J > 0.25f)) return false;   // 1 + b j > 0 on [0, J]
+    int32_t jh = T.J;
+    const float p0s[2] = { u, v };
+    const DF as[2] = { Au, Av };
+    const float hi[2] = { (float)(T.nx - 1), (float)(T.ny - 1) };
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float a = as[k].hi;
+        if (a == 0.0f) continue;
+        const float d = (a > 0.0f ? hi[k] : 0.0f) - p0s[k];    // exact: integers
+        const float den = a - b.hi * d;
+        const float jf = den != 0.0f ? d / den : INFINITY;
+        const float margin = 1e-6f * fabsf(jf) + 1e-3f;
+        if (den > 0.0f && jf >= 0.0f) {
+            if (jf >= (float)T.J + margin) continue;
+            const float fl = floorf(jf), fr = jf - fl;
+            if (fr > margin && fr < 1.0f - margin && jf < (float)T.J) {
+                jh = min(jh, (int32_t)fl);
+                continue;
+            }
+        }
+        const double ad = df_to_double(as[k]), bd = df_to_double(b), dd = (double)d;
+        int32_t jc = !(jf < (float)T.J) ? T.J : (jf < 0.0f ? 0 : (int32_t)floorf(jf));
+#define SS_IN(j) (ad > 0.0 ? (ad * (double)(j) <= dd * fma(bd, (double)(j), 1.0)) \
+                           : (ad * (double)(j) >= dd * fma(bd, (double)(j), 1.0)))
+        int steps = 0;
+        while (jc < T.J && SS_IN(jc + 1) && steps < 3) { ++jc; ++steps; }
+        while (jc >= 1 && !SS_IN(jc) && steps < 3) { --jc; ++steps; }
+        const bool ok = (jc == 0 || SS_IN(jc)) && (jc == T.J || !SS_IN(jc + 1));
+#undef SS_IN
+        if (!ok) return false;
+        jh = min(jh, jc);
+    }
+    j_hi = jh;
+    return true;
+}
+
+// Split a float-float value like split8: hi keeps 8 significant bits (j * hi
+// exact for j < 2^16), lo the rest rounded once.
+__device__ __forceinline__ void split8_df(DF a, float& hi, float& lo) {
+    hi = __int_as_float(__float_as_int(a.hi) & (int)0xFFFF0000u);
+    lo = __fadd_rn(__fsub_rn(a.hi, hi), a.lo);   // a.hi - hi is exact
+}
+
+// Setup of a grid ray (origin at texel (u, v), height h) on a gnomonic tile
+// without FP64 on the common path: the per-sample slope and the projective
+// coefficient in float-float (the same formulas as make_rayf_gnomonic:
+// m = |(X, Y, R)|, f = delta m / (R + h), a = f (R s_xy - s_z (X, Y)) / (g R),
+// b = f s_z / R), the exit sample from the float estimate; FP64 only when
+// that estimate is in doubt or the exit cannot be found that way.
+__device__ __forceinline__ void make_rayf_gnomonic_grid(const Tile& T, int32_t u, int32_t v,
+                                                        float h, float span, RayF& r,
+                                                        float& sin_e) {
+    const float uf = (float)u, vf = (float)v;
+    const DF g = { T.g_hi, T.g_lo };
+    const DF Xp = df_mul_f(g, __fsub_rn(uf, (float)T.cx));   // u - cx exact (half-integers)
+    const DF Yp = df_mul_f(g, __fsub_rn(vf, (float)T.cy));
+    const DF m2 = df_add(df_add(df_mul(Xp, Xp), df_mul(Yp, Yp)), DF{ T.RR_hi, T.RR_lo });
+    const DF rho = df_add(DF{ T.R_f, T.R_lo }, DF{ h, 0.0f });
+    const DF f = df_mul(DF{ T.delta_hi, T.delta_lo }, df_div(df_sqrt(m2), rho));
+    const DF k = df_mul(f, DF{ T.igR_hi, T.igR_lo });
+    const DF sz = { T.sz_f, T.sz_lo };
+    const DF Au = df_mul(k, df_add(DF{ T.Rsx_hi, T.Rsx_lo }, df_neg(df_mul(sz, Xp))));
+    const DF Av = df_mul(k, df_add(DF{ T.Rsy_hi, T.Rsy_lo }, df_neg(df_mul(sz, Yp))));
+    const DF b = df_mul_f(f, T.szR_f);
+    const float Xf = (uf - (float)T.cx) * (float)T.g, Yf = (vf - (float)T.cy) * (float)T.g;
+    const float imf = rsqrtf(Xf * Xf + Yf * Yf + T.R_f * T.R_f);
+    const float se = (Xf * T.sx_f + Yf * T.sy_f + T.R_f * T.sz_f) * imf;
+    const float rhof = T.R_f + h;
+    sin_e = se;
+    r.iu0 = u;
+    r.iv0 = v;
+    r.u0 = uf;
+    r.v0 = vf;
+    split8_df(Au, r.au_hi, r.au_lo);
+    split8_df(Av, r.av_hi, r.av_lo);
+    r.b = b.hi;
+    r.B = 2.0f * rhof * se;
+    r.inv_2rho = 0.5f / rhof;
+    r.inv_rho2 = inv_rho2_of(r.inv_2rho);
+    r.X = 0.0f;
+    r.href = h;
+    r.tv = se < 0.0f ? -rhof * se : -1.0f;
+    r.guard0 = span;
+    r.bu = r.bv = r.inv8r = 0.0f;
+    r.au = __fadd_rn(r.au_hi, r.au_lo);
+    r.av = __fadd_rn(r.av_hi, r.av_lo);
+    r.j_lo = 1;
+    if (!exit_fast_df(T, uf, vf, Au, Av, b, r.j_hi)) {
+        Geom64 G;
+        G.up = (double)u;
+        G.vp = (double)v;
+        G.Au = df_to_double(Au);
+        G.Av = df_to_double(Av);
+        G.b = df_to_double(b);
+        sample_range(T, G, r.j_lo, r.j_hi);
+    }
+    const float amax = fmaxf(fabsf(r.au), fabsf(r.av));
+    r.pos_eps = 1e-3f + 5e-7f * (float)(T.nx + T.ny) + 8e-7f * amax * (float)max(r.j_hi, 1);
+    set_gconst(T, r);
 }
 
 // Float32 ray setup for gnomonic tiles.  FP64 only where float32 is not

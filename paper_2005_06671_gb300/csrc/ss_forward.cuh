@@ -66,6 +66,12 @@ __device__ __forceinline__ int32_t draw_strip(int32_t n_strips, int32_t* s_next,
     return my < n_strips ? my : -1;
 }
 
+// Seed-table column of local ray r >= 0: its column in a rectangular chunk, or
+// its virtual column (LH consecutive ids each) in a run of listed rays.
+__device__ __forceinline__ int32_t seed_col(const ChunkRange& P, int32_t r, int32_t LH) {
+    return (int32_t)(P.rect ? (uint32_t)r % (uint32_t)P.w : (uint32_t)r / (uint32_t)LH);
+}
+
 // ---------------------------------------------------------------- descent
 // Exact walks (light-only walks: dp_light_kernel below).
 // Column seeds (grid rays in rectangles of at most kColSeedMaxW columns, the
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
                 finish_ray<kStereo, true>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
                                     w.nb, w.nl);
                 if (colseed && w.bestj > 0) {
-                    const int32_t c = P.rect ? r % P.w : r / LH;
+                    const int32_t c = seed_col(P, r, LH);
                     s_seed[c] = w.bestj;
                     if (kGrid) {
                         s_su[c] = rf.u0;
@@ -173,9 +179,10 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_forward_kernel(cons
                         left = st.count - 1;
                         fresh = true;
                         if (colseed) {                   // a ray above in this column
-                            prev_j = s_seed[r % P.w];
-                            su = s_su[r % P.w];
-                            sv = s_sv[r % P.w];
+                            const int32_t c = seed_col(P, r, LH);
+                            prev_j = s_seed[c];
+                            su = s_su[c];
+                            sv = s_sv[c];
                         }
                     }
                 }
@@ -284,7 +291,7 @@ dp_light_kernel(const __grid_constant__ FwdArgs a) {
                 finish_ray<kStereo, true>(a.T, a.R, a.O, chunk_ray(P, a.T.nx, r), w.best, w.bestj,
                                           w.nb, w.nl);
                 if (colseed && w.bestj > 0) {
-                    const int32_t c = P.rect ? r % P.w : r / LH;
+                    const int32_t c = seed_col(P, r, LH);
                     s_seed[c] = w.bestj;
                     if (kGrid) {
                         s_su[c] = rf.u0;
@@ -322,7 +329,7 @@ dp_light_kernel(const __grid_constant__ FwdArgs a) {
                 r = (int32_t)q[kWr][slot];
                 if (r >= 0) {
                     Pack::load(q, slot, rf);
-                    const int32_t c = P.rect ? r % P.w : r / LH;
+                    const int32_t c = seed_col(P, r, LH);
                     const int32_t prev_j = colseed ? s_seed[c] : -1;
                     const bool near = prev_j > 0;
                     const int32_t jc = !near ? -1

@@ -25,9 +25,10 @@ __device__ __forceinline__ float cos_elev_f32(const Tile& T, const Rays& R, int6
                                               bool stereo) {
     float u, v;
     if (R.mode == 0) {
-        const int64_t vv = r / T.nx;
-        u = (float)(r - vv * T.nx);
-        v = (float)vv;
+        int32_t iu, iv;
+        grid_uv(T, r, iu, iv);
+        u = (float)iu;
+        v = (float)iv;
     } else {
         u = R.uv[2 * r];
         v = R.uv[2 * r + 1];
@@ -105,12 +106,22 @@ __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t 
     double up, vp, hp, href;
     float uf, vf;
     if (kGrid) {
-        const int64_t v = r / T.nx, u = r - v * T.nx;
+        int32_t u, v;
+        grid_uv(T, r, u, v);
+        if (!kStereo) {   // no FP64 on the common path
+            float se;
+            make_rayf_gnomonic_grid(T, u, v, T.h[(int64_t)v * T.pitch + u], span, rf, se);
+            if (kLight) {
+                const float ce = sqrtf(fmaxf(0.0f, 1.0f - se * se));
+                rf.c_sat = ce > 0.0f ? 1.002f * T.alpha_f / ce : INFINITY;
+            }
+            return;
+        }
         uf = (float)u;
         vf = (float)v;
         up = (double)u;
         vp = (double)v;
-        hp = href = (double)T.h[v * T.pitch + u];
+        hp = href = (double)T.h[(int64_t)v * T.pitch + u];
     } else {
         double ow[4];
         int32_t oi0, oj0;
@@ -264,7 +275,7 @@ __device__ __forceinline__ ChunkRange chunk_range(int64_t c, int64_t n, int32_t 
 
 __device__ __forceinline__ int64_t chunk_ray(const ChunkRange& C, int32_t nx, int32_t i) {
     if (!C.rect) return C.lo + i;
-    const int32_t q = i / C.w;
+    const int32_t q = (int32_t)((uint32_t)i / (uint32_t)C.w);   // i >= 0
     return (int64_t)(C.y0 + q) * nx + C.x0 + (i - q * C.w);
 }
 
