@@ -37,7 +37,7 @@ UNIT = "rays/s"
 CONFIG = "mid"
 # dram__bytes_read.sum + dram__bytes_write.sum of one dp_forward_kernel launch on
 # the 4096x4096 workload (ncu, one pass); None until taken for the current kernel
-MID_DP_TRAFFIC_BYTES = None
+MID_DP_TRAFFIC_BYTES = 92141056 + 90589440
 
 
 def parse_args(argv=None):
