@@ -141,8 +141,7 @@ typedef struct {
                               the last finished ray of its column (grid rays:
                               columns of the ray rectangle; listed rays: a
                               block's ids read as 256 columns of consecutive
-                              ids; listed rays in light-only mode: no
-                              seeding).
+                              ids).
                               S in [2, 256]: each lane walks a strip of S
                               neighbouring rays (down a rectangle column, or
                               consecutive ids), seeding from the previous one.

@@ -213,10 +213,8 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     // ray rectangles, each seeded from the last finished ray of its column
     // (column seeds, window +-1, leaf level 1); listed rays are read as 256
     // columns of consecutive ids and drawn the same way (window +-2: adjacent
-    // view rays can be several texels apart; leaf level 2), except in
-    // light-only mode where they stay unseeded (measured faster on the polar
-    // view, whose lit rays end at the root).  Uniform stepping draws single
-    // rays from row-major runs.
+    // view rays can be several texels apart; leaf level 2).  Uniform stepping
+    // draws single rays from row-major runs.
     int block = params->block_threads ? params->block_threads : 256;
     const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread
                         : !descent                     ? 16
@@ -231,7 +229,7 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
         a.tile_w = kDefaultTileW;
     if (a.tile_w > 0 && a.rays_per_block % a.tile_w != 0) return SS_ERR_INVALID_ARG;
     a.colseed = (descent && params->strip_len == 0 &&
-                 (rays->mode == SS_RAYS_GRID ? a.tile_w <= ss::kColSeedMaxW : !light_only))
+                 (rays->mode != SS_RAYS_GRID || a.tile_w <= ss::kColSeedMaxW))
                     ? 1 : 0;
     // strips: explicit strip_len, else (no column seeds) strips of kDefaultStrip,
     // none in light-only mode

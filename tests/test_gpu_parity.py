@@ -345,3 +345,37 @@ def test_light_only_mode_vs_oracle(name, n):
                                r // h.shape[1])
             j = lo["argmin"][r]
             assert j >= 1 and cs[j - 1] * math.sqrt(1 - sinp[r] ** 2) <= -inst["alpha"]
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(rays_per_thread=1, refill_min=1),
+                                dict(rays_per_thread=3, refill_min=2, ray_tile_w=8),
+                                dict(rays_per_thread=7, block_threads=64),
+                                dict(rays_per_thread=5, block_threads=96, refill_min=32),
+                                dict(strip_len=4), dict(seed_width=4, leaf_level=3)])
+def test_light_only_descent_launch_shapes(kw):
+    """The light-only descent (per-warp queues of parked rays) under odd launch
+    shapes: tiny chunks, partial warps and blocks, eager and lazy refills,
+    ragged rectangles, grid and listed rays.  Every ray is written (outputs are
+    pre-filled with sentinels); the light equals the exact descent's bit for
+    bit and so does the argmin of every penumbra ray."""
+    h = lunar_tile(130, 12.0, seed=91, amplitude=700.0, n_craters=6, ny=77)
+    hf = ss.Heightfield(_dev(h), 12.0, R)
+    mip = ss.ss_build_maxmip(hf)
+    # a 2 degree disc for wide penumbrae (the oracle finds 146 grid and 41 listed ones)
+    sun = ss.Sun(math.radians(1.1), math.radians(140.0), math.radians(2.0))
+    uv = random_origins(3001, 130, 77, seed=17)
+    for uvt in (None, _dev(uv)):
+        n = h.size if uvt is None else uv.shape[0]
+        out = dict(light=torch.full((n,), -7.0, device="cuda"),
+                   argmin=torch.full((n,), -7, dtype=torch.int32, device="cuda"))
+        lo = ss.ss_shadow_forward(hf, mip, sun, 3000.0, uv=uvt, light_only=True, want_cost=False,
+                                  out=out, **kw)
+        ex = ss.ss_shadow_forward(hf, mip, sun, 3000.0, uv=uvt)
+        torch.cuda.synchronize()
+        light, arg = lo["light"].cpu().numpy(), lo["argmin"].cpu().numpy()
+        el, ea = ex["light"].cpu().numpy(), ex["argmin"].cpu().numpy()
+        assert np.all(light >= 0.0) and np.all(arg != -7)
+        assert np.array_equal(light.view(np.uint32), el.view(np.uint32))
+        pen = (el > 0) & (el < 1)
+        assert pen.sum() > 30
+        assert np.array_equal(arg[pen], ea[pen])
