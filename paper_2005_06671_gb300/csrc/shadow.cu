@@ -104,13 +104,24 @@ __global__ void __launch_bounds__(256) backward_kernel(const BwdArgs a) {
     for (int64_t base = (int64_t)blockIdx.x * chunk; base < n; base += (int64_t)gridDim.x * chunk) {
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
+        // all loads of the round first (independent, in flight together), then the tests
+        int32_t jj[kBwdRounds];
+        float gg[kBwdRounds], cc[kBwdRounds];
+#pragma unroll
         for (int k = 0; k < kBwdRounds; ++k) {
             const int64_t r = base + (int64_t)k * blockDim.x + threadIdx.x;
-            if (r >= n) break;
-            if (a.argmin[r] < 1 || a.grad_light[r] == 0.0f) continue;
+            const bool in = r < n;
+            jj[k] = in ? a.argmin[r] : 0;
+            gg[k] = in ? a.grad_light[r] : 0.0f;
+            cc[k] = (in && a.cost) ? a.cost[r] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kBwdRounds; ++k) {
+            const int64_t r = base + (int64_t)k * blockDim.x + threadIdx.x;
+            if (jj[k] < 1 || gg[k] == 0.0f) continue;
             // the forward's float32 cost rules out rays whose light is certainly
             // saturated (the same test the forward uses before its FP64 re-evaluation)
-            if (a.cost && fabsf(a.cost[r]) * cos_elev_f32(a.T, a.R, r, a.T.proj != 0) >=
+            if (a.cost && fabsf(cc[k]) * cos_elev_f32(a.T, a.R, r, a.T.proj != 0) >=
                               1.001f * a.T.alpha_f)
                 continue;
             s_ray[atomicAdd(&s_cnt, 1)] = r;
