@@ -139,9 +139,9 @@ typedef struct {
                               minimum, so results are unchanged).  0 = default:
                               single rays drawn row by row, each seeded from
                               the last finished ray of its column (grid rays:
-                              columns of the ray rectangle; listed rays: a
-                              block's ids read as 256 columns of consecutive
-                              ids).
+                              columns of the ray rectangle, at most 512 wide,
+                              else strips of 10; listed rays: a block's ids
+                              read as 256 columns of consecutive ids).
                               S in [2, 256]: each lane walks a strip of S
                               neighbouring rays (down a rectangle column, or
                               consecutive ids), seeding from the previous one.
@@ -153,7 +153,9 @@ typedef struct {
                               above, any other value = no seeding.  Other
                               calls ignore it.                                 */
     int32_t seed_width;    /* seeded descents: a ray seeded from a neighbour's
-                              argmin j evaluates its samples j-w..j+w, w in
+                              argmin j evaluates its samples within +-w of
+                              where j's terrain point lies along this ray
+                              (grid rays; listed rays: of j itself), w in
                               [0, 16]; 0 = default (grid rays 1, listed
                               rays 2: neighbouring view rays can be several
                               texels apart)                                    */
