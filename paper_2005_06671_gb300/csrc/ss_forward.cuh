@@ -1,6 +1,7 @@
-// Forward kernels (exact max-mip descent and uniform stepping), templated on
-// the tile mapping; fwd_gnomonic.cu and fwd_stereo.cu each instantiate one
-// mapping so the two compile in parallel.
+// Forward kernels (exact max-mip descent, light-only descent, uniform
+// stepping, and the FP64 re-evaluation of penumbra rays), templated on the
+// tile mapping; fwd_gnomonic.cu and fwd_stereo.cu each instantiate one mapping
+// so the two compile in parallel.
 //
 // Work decomposition: one thread walks one shadow ray at a time; each block
 // owns a contiguous range of ray ids (grid mode: row-major texels, so a warp's
@@ -24,7 +25,8 @@ namespace ss {
 #define SS_FWD_MIN_BLOCKS 4
 #endif
 
-// Scheduling shared by both forward kernels.  Block b owns rays
+// Scheduling of the exact descent and uniform stepping (the light-only descent
+// parks set-up rays first, see dp_light_kernel).  Block b owns rays
 // [b*rays_per_block, ...) (the grid oversubscribes the SMs so the hardware
 // block scheduler balances them).  Each lane walks one ray.  A lane whose ray
 // is finished keeps its result in registers and waits; once at least
