@@ -138,11 +138,15 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                 if (r >= 0) {
                     setup_ray<true, kLight>(D.T, grid_rays, L.ray, S.span, rf);
                     const bool near = prev_j > 0;
-                    const int32_t jc = near ? seed_centre(rf, prev_j, su - rf.u0, sv - rf.v0) : -1;
+                    const int32_t jc =
+                        near ? seed_centre(rf, prev_j, su - rf.u0, sv - rf.v0) : -1;
                     int32_t sj, n_seed;
                     const float sc =
-                        D.poly ? seed_ray<true, true, false>(D.T, rf, near, jc, a.seed_w, false, sj, n_seed)
-                               : seed_ray<true, false, false>(D.T, rf, near, jc, a.seed_w, false, sj, n_seed);
+                        D.poly
+                            ? seed_ray<true, true, false>(D.T, rf, near, jc, a.seed_w, false, sj,
+                                                          n_seed)
+                            : seed_ray<true, false, false>(D.T, rf, near, jc, a.seed_w, false, sj,
+                                                           n_seed);
                     if (sj > 0) {
                         walk_begin_seeded<kLight>(w, rf, a.kleaf, sc, sj);
                         if (kCount) w.nl = n_seed;
@@ -168,15 +172,18 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                         setup_ray<true, kLight>(D.T, grid_rays, L.ray, S.span, rf);
                         const int32_t pj = S.colseed ? seeds[L.slot] : -1;
                         const bool near = pj > 0;
-                        const int32_t jc =
-                            near ? seed_centre(rf, pj, seed_u[L.slot] - rf.u0, seed_v[L.slot] - rf.v0)
-                                 : -1;
+                        const int32_t jc = near ? seed_centre(rf, pj, seed_u[L.slot] - rf.u0,
+                                                              seed_v[L.slot] - rf.v0)
+                                                : -1;
                         // seeded modes: a ray with no finished neighbour takes sparse samples
                         const bool geo = !kLight && (S.colseed || a.strip > 1);
                         int32_t sj, n_seed;
                         const float sc =
-                            D.poly ? seed_ray<true, true, false>(D.T, rf, near, jc, a.seed_w, geo, sj, n_seed)
-                                   : seed_ray<true, false, false>(D.T, rf, near, jc, a.seed_w, geo, sj, n_seed);
+                            D.poly
+                                ? seed_ray<true, true, false>(D.T, rf, near, jc, a.seed_w, geo,
+                                                              sj, n_seed)
+                                : seed_ray<true, false, false>(D.T, rf, near, jc, a.seed_w, geo,
+                                                               sj, n_seed);
                         if (sj > 0) {
                             walk_begin_seeded<kLight>(w, rf, a.kleaf, sc, sj);
                             if (kCount) w.nl = n_seed;

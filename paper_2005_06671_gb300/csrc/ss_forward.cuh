@@ -313,7 +313,8 @@ dp_light_kernel(const __grid_constant__ FwdArgs a) {
                 const int m = max(0, min(want, n_order - base));
                 if (lane < m) {
                     const int32_t o = base + lane;
-                    const int32_t e = LW > 0 ? (o % LW) * LH + o / LW : o;   // virtual column o % LW
+                    // listed rays: virtual column o % LW
+                    const int32_t e = LW > 0 ? (o % LW) * LH + o / LW : o;
                     const int slot = (qh + qn + lane) % kQSlots;
                     if (e < P.cnt)
                         park_ray<kGrid, kStereo>(a, chunk_ray(P, a.T.nx, e), span, q, slot);
@@ -334,9 +335,10 @@ dp_light_kernel(const __grid_constant__ FwdArgs a) {
                     const int32_t c = seed_col(P, r, LH);
                     const int32_t prev_j = colseed ? s_seed[c] : -1;
                     const bool near = prev_j > 0;
-                    const int32_t jc = !near ? -1
-                                       : kGrid ? seed_centre(rf, prev_j, s_su[c] - rf.u0, s_sv[c] - rf.v0)
-                                               : prev_j;
+                    const int32_t jc =
+                        !near   ? -1
+                        : kGrid ? seed_centre(rf, prev_j, s_su[c] - rf.u0, s_sv[c] - rf.v0)
+                                : prev_j;
                     int32_t sj, n_seed;
                     const float sc = seed_ray<kGrid, kPoly, kStereo>(a.T, rf, near, jc, a.seed_w,
                                                                      false, sj, n_seed);
