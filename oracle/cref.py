@@ -60,9 +60,14 @@ def _load():
                                          p, i64]
             lib.or_sin_elev.restype = None
             lib.or_sin_elev.argtypes = [p, i32, i32, i64, d, d, i32, d, d, i32, i64, p, p]
+            lib.or_shadow_svec.restype = None
+            lib.or_shadow_svec.argtypes = [p, i32, i32, i64, d, d, i32, p, d, d, d, i32, i64,
+                                           p, p, p, p, p, p]
+            lib.or_sun_vector.restype = None
+            lib.or_sun_vector.argtypes = [d, d, p]
             lib.or_grad.restype = None
             lib.or_grad.argtypes = [p, i32, i32, i64, d, d, i32, d, d, d, d, i32, i64, p, p,
-                                    p, p, p, p]
+                                    p, p, p, p, p, p]
             lib.or_maxmip.restype = i32
             lib.or_maxmip.argtypes = [p, i32, i32, i64, p]
             lib.ov_view_hits.restype = None
@@ -126,6 +131,37 @@ def shadow(h, g, radius, elev, az, alpha, lmax, step_texels=0.5, proj="gnomonic"
     return light, argmin, cost
 
 
+def sun_vector(elev, az):
+    """Unit sun direction (cos e sin a, cos e cos a, sin e) in the tile frame."""
+    out = np.empty(3, np.float64)
+    _load().or_sun_vector(float(elev), float(az), _ptr(out))
+    return out
+
+
+def shadow_svec(h, g, radius, svec, alpha, lmax, step_texels=0.5, proj="gnomonic",
+                uv=None, lift=None):
+    """Brute-force forward with the light direction given as a 3-vector ``svec``
+    (used as is, not normalised), plus the runner-up cost of each ray.
+
+    Returns (light, argmin, cost, cost2): cost2 is the smallest cost over the
+    usable samples other than the argmin (+inf with fewer than two samples).
+    """
+    lib = _load()
+    h64 = _heights(h)
+    ny, nx = h64.shape
+    mode, n, uv, lift = _rays(uv, lift)
+    nr = nx * ny if mode == 0 else n
+    sv = np.ascontiguousarray(svec, dtype=np.float64).reshape(3)
+    light = np.empty(nr, np.float64)
+    argmin = np.empty(nr, np.int64)
+    cost = np.empty(nr, np.float64)
+    cost2 = np.empty(nr, np.float64)
+    lib.or_shadow_svec(_ptr(h64), nx, ny, nx, float(g), float(radius), PROJ[proj], _ptr(sv),
+                       float(alpha), float(lmax), float(step_texels), mode, n, _ptr(uv),
+                       _ptr(lift), _ptr(light), _ptr(argmin), _ptr(cost), _ptr(cost2))
+    return light, argmin, cost, cost2
+
+
 def ray_costs(h, g, radius, elev, az, lmax, u, v, lift=0.0, step_texels=0.5,
               proj="gnomonic"):
     """Cost of every sample j = 1..J along one ray (NaN where outside the tile)."""
@@ -153,11 +189,13 @@ def sin_elev(h, g, radius, elev, az, proj="gnomonic", uv=None):
 
 
 def grad(h, g, radius, elev, az, alpha, argmin, gL, step_texels=0.5, proj="gnomonic",
-         uv=None, lift=None):
+         uv=None, lift=None, with_abs=False):
     """Analytic gradient of sum(gL * light) at the given argmin.
 
     Returns (grad_h float64 [ny, nx], grad_sun float64 [5] =
-    (d/d elev, d/d az, d/ds_x, d/ds_y, d/ds_z)).
+    (d/d elev, d/d az, d/ds_x, d/ds_y, d/ds_z)); with ``with_abs`` also
+    (abs_h, cnt_h) [ny, nx]: per texel the sum of |contribution| over the
+    non-zero per-ray contributions, and their number.
     """
     lib = _load()
     h64 = _heights(h)
@@ -167,9 +205,13 @@ def grad(h, g, radius, elev, az, alpha, argmin, gL, step_texels=0.5, proj="gnomo
     gL = np.ascontiguousarray(gL, dtype=np.float64)
     gh = np.zeros((ny, nx), np.float64)
     gs = np.zeros(5, np.float64)
+    ah = np.zeros((ny, nx), np.float64) if with_abs else None
+    ch = np.zeros((ny, nx), np.float64) if with_abs else None
     lib.or_grad(_ptr(h64), nx, ny, nx, float(g), float(radius), PROJ[proj], float(elev),
                 float(az), float(alpha), float(step_texels), mode, n, _ptr(uv), _ptr(lift),
-                _ptr(argmin), _ptr(gL), _ptr(gh), _ptr(gs))
+                _ptr(argmin), _ptr(gL), _ptr(gh), _ptr(gs), _ptr(ah), _ptr(ch))
+    if with_abs:
+        return gh, gs, ah, ch
     return gh, gs
 
 

@@ -199,14 +199,17 @@ static int sample_cost(const or_tile* t, const or_origin* o, const double s[3],
     return 1;
 }
 
+/* cost2 (may be NULL): the runner-up, the smallest cost over the usable
+ * samples other than the argmin (+inf with fewer than two), so that a caller
+ * can tell a unique minimum from a tie. */
 static void ray_forward(const or_tile* t, const or_sun* sun, const double s[3],
                         double lmax, double step_texels, double u, double v, double lift,
-                        double* light, int64_t* argmin, double* cost) {
+                        double* light, int64_t* argmin, double* cost, double* cost2) {
     or_origin o;
     make_origin(t, u, v, lift, &o);
     double delta = step_texels * t->g;
     int64_t J = n_samples(lmax, delta);
-    double best = INFINITY;
+    double best = INFINITY, second = INFINITY;
     int64_t bj = -1;
     int seen = 0;
     for (int64_t j = 1; j <= J; ++j) {
@@ -214,8 +217,11 @@ static void ray_forward(const or_tile* t, const or_sun* sun, const double s[3],
         if (sample_cost(t, &o, s, (double)j * delta, &c)) {
             seen = 1;
             if (c < best) {
+                second = best;
                 best = c;
                 bj = j;
+            } else if (c < second) {
+                second = c;
             }
         } else if (seen) {
             break;   /* the ray has left the tile: it is not followed further */
@@ -225,6 +231,7 @@ static void ray_forward(const or_tile* t, const or_sun* sun, const double s[3],
     double ce = sqrt(fmax(0.0, 1.0 - se * se));
     *argmin = bj;
     *cost = best;
+    if (cost2) *cost2 = second;
     if (bj < 0) { *light = 1.0; return; }
     double d = best * ce / sun->alpha;
     if (d > 1.0) d = 1.0;
@@ -245,6 +252,12 @@ static void ray_origin_coords(const or_tile* t, int32_t mode, int64_t r, const f
     }
 }
 
+/* sun direction of elevation e and azimuth a (tile-centre frame) */
+void or_sun_vector(double elev, double az, double* out) {
+    or_sun sun = { elev, az, 0.0 };
+    sun_dir(&sun, out);
+}
+
 /* ---- exported API --------------------------------------------------------------
  * heights: double [ny][pitch]; mode 0 = one ray per texel centre (n = nx*ny, ray r
  * at (r % nx, r / nx)); mode 1 = list of n origins uv[2n] (floats, texel coords)
@@ -262,7 +275,31 @@ void or_shadow(const double* h, int32_t nx, int32_t ny, int64_t pitch, double g,
     for (int64_t r = 0; r < nr; ++r) {
         double u, v, l;
         ray_origin_coords(&t, mode, r, uv, lift, &u, &v, &l);
-        ray_forward(&t, &sun, s, lmax, step_texels, u, v, l, &light[r], &argmin[r], &cost[r]);
+        ray_forward(&t, &sun, s, lmax, step_texels, u, v, l, &light[r], &argmin[r], &cost[r],
+                    NULL);
+    }
+}
+
+/* The same forward with the light direction given as a 3-vector s (used as
+ * is, not normalised: q = p + t s, sin(eps_p) = n_p . s) instead of elevation
+ * and azimuth, so that the light can be differentiated along each component of
+ * s as a free vector; and with the runner-up cost of every ray (cost2, may be
+ * NULL; see ray_forward). */
+void or_shadow_svec(const double* h, int32_t nx, int32_t ny, int64_t pitch, double g, double R,
+                    int32_t proj, const double* svec, double alpha, double lmax,
+                    double step_texels, int32_t mode, int64_t n, const float* uv,
+                    const float* lift, double* light, int64_t* argmin, double* cost,
+                    double* cost2) {
+    or_tile t = { h, nx, ny, pitch, g, R, proj };
+    or_sun sun = { 0.0, 0.0, alpha };
+    const double s[3] = { svec[0], svec[1], svec[2] };
+    int64_t nr = (mode == 0) ? (int64_t)nx * ny : n;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < nr; ++r) {
+        double u, v, l;
+        ray_origin_coords(&t, mode, r, uv, lift, &u, &v, &l);
+        ray_forward(&t, &sun, s, lmax, step_texels, u, v, l, &light[r], &argmin[r], &cost[r],
+                    cost2 ? &cost2[r] : NULL);
     }
 }
 
@@ -311,7 +348,10 @@ void or_sin_elev(const double* h, int32_t nx, int32_t ny, int64_t pitch, double 
  * Analytic gradient of  L = sum_r gL[r] * light[r]  at the given per-ray argmin
  * (1-based sample index, -1 = none).  Accumulates dL/dh into grad_h [ny][pitch]
  * and writes grad_sun[5] = (dL/d elev, dL/d az, dL/ds_x, dL/ds_y, dL/ds_z), the
- * last three with s treated as a free 3-vector.
+ * last three with s treated as a free 3-vector.  grad_h_abs and grad_h_cnt
+ * (both [ny][pitch], may be NULL) accumulate, per texel, the sum of the absolute
+ * values of the non-zero per-ray contributions and their number, the scale of
+ * the rounding of a float32 accumulation of the same terms.
  *
  * light = F(d), d = c cos(eps)/alpha (clamped: zero gradient outside (-1, 1)),
  * F'(d) = (2/pi) sqrt(1 - d^2).
@@ -321,7 +361,8 @@ void or_sin_elev(const double* h, int32_t nx, int32_t ny, int64_t pitch, double 
 void or_grad(const double* h, int32_t nx, int32_t ny, int64_t pitch, double g, double R,
              int32_t proj, double elev, double az, double alpha, double step_texels,
              int32_t mode, int64_t n, const float* uv, const float* lift,
-             const int64_t* argmin, const double* gL, double* grad_h, double* grad_sun) {
+             const int64_t* argmin, const double* gL, double* grad_h, double* grad_sun,
+             double* grad_h_abs, double* grad_h_cnt) {
     or_tile t = { h, nx, ny, pitch, g, R, proj };
     or_sun sun = { elev, az, alpha };
     double s[3];
@@ -360,14 +401,22 @@ void or_grad(const double* h, int32_t nx, int32_t ny, int64_t pitch, double g, d
         /* sample texels: dc/dh_k = -w_k / t* */
         int64_t idx[4] = { b.j0 * pitch + b.i0, b.j0 * pitch + b.i0 + 1,
                            (b.j0 + 1) * pitch + b.i0, (b.j0 + 1) * pitch + b.i0 + 1 };
-        for (int k = 0; k < 4; ++k) grad_h[idx[k]] += gc * (-b.w[k] / ts);
+        for (int k = 0; k < 4; ++k) {
+            double x = gc * (-b.w[k] / ts);
+            grad_h[idx[k]] += x;
+            if (grad_h_abs && x != 0.0) { grad_h_abs[idx[k]] += fabs(x); grad_h_cnt[idx[k]] += 1.0; }
+        }
         /* origin texels: dc/dh_p = (dH/dq - dh/dq) . n_p / t*  */
         double dHq[3] = { q[0] / qn, q[1] / qn, q[2] / qn };
         double dcdhp = ((dHq[0] - dhq[0]) * o.n[0] + (dHq[1] - dhq[1]) * o.n[1] +
                         (dHq[2] - dhq[2]) * o.n[2]) / ts;
         int64_t oidx[4] = { o.ob.j0 * pitch + o.ob.i0, o.ob.j0 * pitch + o.ob.i0 + 1,
                             (o.ob.j0 + 1) * pitch + o.ob.i0, (o.ob.j0 + 1) * pitch + o.ob.i0 + 1 };
-        for (int k = 0; k < 4; ++k) grad_h[oidx[k]] += gc * dcdhp * o.ob.w[k];
+        for (int k = 0; k < 4; ++k) {
+            double x = gc * dcdhp * o.ob.w[k];
+            grad_h[oidx[k]] += x;
+            if (grad_h_abs && x != 0.0) { grad_h_abs[oidx[k]] += fabs(x); grad_h_cnt[oidx[k]] += 1.0; }
+        }
         /* sun: dc/ds = (dH/dq - dh/dq) (q depends on s through t* s), plus the
          * cos(eps) factor of d: dd/ds = (c/alpha) * (-se/ce) * n_p */
         for (int i = 0; i < 3; ++i) {

@@ -310,6 +310,111 @@ def test_grad_matches_central_differences(proj):
     assert checked >= 20
 
 
+@pytest.mark.parametrize("proj", ["gnomonic", "polar_stereo"])
+def test_grad_sun_vector_matches_central_differences(proj):
+    """The raw sun-direction gradient grad_sun[2:5] (s a free 3-vector: q = p + t s
+    and sin(eps_p) = n_p . s, both linear in s) against central differences of
+    the forward taken along each component of s and along s itself (the
+    direction the elevation/azimuth pins above cannot see, since both of their
+    tangents are orthogonal to s).  Rays with a unique argmin (runner-up cost at
+    least 1e-4 rad above the minimum, from the oracle's own runner-up output) and
+    |d| < 0.98; step 1e-5 moves any sample cost by ~1e-5 rad (|dc/ds| ~ 1 + terrain
+    slope), below that gap, and the argmin is asserted unchanged.  Near |d| = 1
+    the third derivative of F(d) = light grows like (1 - d^2)^-1.5, so the
+    central difference's eps^2 error reaches ~2e-5 relative there; Richardson's
+    extrapolation of the steps eps and eps/2, (4 D(eps/2) - D(eps)) / 3, removes
+    that term."""
+    g, lmax = 20.0, 1500.0
+    elev, az = math.radians(2.0), math.radians(57.0)
+    alpha = math.radians(3.0)
+    h = _fd_case(31, proj)
+    n = 1200
+    uv = random_origins(n, 40, 40, seed=34, margin=1.0)
+    lift = np.random.default_rng(35).uniform(0, 5, n).astype(np.float32)
+    s = oracle.sun_vector(elev, az)
+    light, argmin, cost, cost2 = oracle.shadow_svec(h, g, R, s, alpha, lmax, proj=proj, uv=uv,
+                                                    lift=lift)
+    # the vector form reproduces the elevation/azimuth form exactly
+    l2, a2, c2 = oracle.shadow(h, g, R, elev, az, alpha, lmax, proj=proj, uv=uv, lift=lift)
+    assert np.array_equal(a2, argmin) and np.array_equal(l2, light)
+    sinp = oracle.sin_elev(h, g, R, elev, az, proj=proj, uv=uv)
+    d = cost * np.sqrt(1 - sinp ** 2) / alpha
+    ok = (argmin > 0) & (np.abs(d) < 0.98) & (cost2 - cost >= 1e-4)
+    ids = np.nonzero(ok)[0]
+    assert ids.size >= 20
+    one_uv, one_lift = uv[ids], lift[ids]
+    gL = np.zeros(ids.size)
+    eps = 1e-5
+    dirs = [np.eye(3)[i] for i in range(3)] + [s]
+    for r_i, r in enumerate(ids):
+        gL[:] = 0.0
+        gL[r_i] = 1.0
+        _, gs = oracle.grad(h, g, R, elev, az, alpha, argmin[ids], gL, proj=proj, uv=one_uv,
+                            lift=one_lift)
+        for e in dirs:
+            dd = []
+            for st in (eps, 0.5 * eps):
+                lp, ap, _, _ = oracle.shadow_svec(h, g, R, s + st * e, alpha, lmax, proj=proj,
+                                                  uv=one_uv[r_i:r_i + 1],
+                                                  lift=one_lift[r_i:r_i + 1])
+                lm, am, _, _ = oracle.shadow_svec(h, g, R, s - st * e, alpha, lmax, proj=proj,
+                                                  uv=one_uv[r_i:r_i + 1],
+                                                  lift=one_lift[r_i:r_i + 1])
+                assert ap[0] == argmin[r] and am[0] == argmin[r]
+                dd.append((lp[0] - lm[0]) / (2 * st))
+            fd = (4.0 * dd[1] - dd[0]) / 3.0
+            an = float(np.dot(gs[2:5], e))
+            assert abs(fd - an) <= 1e-5 * abs(an) + 1e-5, (r, e, fd, an)
+
+
+def test_runner_up_cost_is_second_smallest_sample_cost():
+    """cost2 of the vector-form forward = the second smallest per-sample cost
+    (brute force over the per-sample costs; equal costs count twice)."""
+    h = lunar_tile(40, 20.0, seed=22, amplitude=600.0, n_craters=5)
+    elev, az = math.radians(1.2), math.radians(75.0)
+    s = oracle.sun_vector(elev, az)
+    light, argmin, cost, cost2 = oracle.shadow_svec(h, 20.0, R, s, ALPHA, 2000.0)
+    rng = np.random.default_rng(1)
+    for r in rng.choice(40 * 40, 60, replace=False):
+        cs = oracle.ray_costs(h, 20.0, R, elev, az, 2000.0, r % 40, r // 40)
+        cs = np.sort(cs[np.isfinite(cs)])
+        if cs.size < 2:
+            assert np.isinf(cost2[r])
+            continue
+        assert cost[r] == cs[0] and cost2[r] == cs[1]
+    # a tile whose every sample ties: the runner-up equals the minimum
+    flat = np.zeros((20, 20))
+    _, _, c, c2 = oracle.shadow_svec(flat, 20.0, R, s, ALPHA, 2000.0)
+    assert np.all(c2 >= c)
+
+
+def test_grad_abs_and_count_outputs():
+    """The per-texel |contribution| sum and count outputs of or_grad: with gL of
+    one sign on a single ray, abs equals |grad| texel by texel on the sample
+    texels; summed over rays, abs >= |grad| and the counts are whole numbers
+    that add up to the non-zero contributions (at most 8 per ray)."""
+    g, lmax = 20.0, 1500.0
+    h = _fd_case(41, "gnomonic")
+    elev, az = math.radians(1.7), math.radians(250.0)
+    alpha = math.radians(3.0)
+    light, argmin, _ = oracle.shadow(h, g, R, elev, az, alpha, lmax)
+    gL = np.random.default_rng(43).normal(size=light.size)
+    gh, gs, ah, ch = oracle.grad(h, g, R, elev, az, alpha, argmin, gL, with_abs=True)
+    gh2, gs2 = oracle.grad(h, g, R, elev, az, alpha, argmin, gL)
+    assert np.array_equal(gh, gh2) and np.array_equal(gs, gs2)
+    assert np.all(ah >= np.abs(gh) * (1 - 1e-12))
+    assert np.all(ch == np.round(ch)) and ch.sum() <= 8 * np.count_nonzero(gL)
+    pen = np.nonzero((light > 0) & (light < 1))[0]
+    assert pen.size > 10
+    assert ch.sum() >= 4 * pen.size
+    r = pen[0]
+    one = np.zeros_like(gL)
+    one[r] = 1.0
+    g1, _, a1, c1 = oracle.grad(h, g, R, elev, az, alpha, argmin, one, with_abs=True)
+    assert np.allclose(a1, np.abs(g1), rtol=1e-12, atol=0)
+    assert 4 <= c1.sum() <= 8
+
+
 def test_grad_is_sum_of_per_ray_gradients():
     g, lmax = 20.0, 1500.0
     h = _fd_case(41, "gnomonic")
