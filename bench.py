@@ -35,9 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "shadow rays/s (DP+maxmip vs uniform stepping, same GB300, <=1e-5 err); fwd+bwd rays/s"
 UNIT = "rays/s"
 CONFIG = "mid"
-# dram__bytes_read.sum + dram__bytes_write.sum of one dp_forward_kernel launch on
-# the 4096x4096 workload (ncu, one pass); None until taken for the current kernel
-MID_DP_TRAFFIC_BYTES = 92141056 + 90589440
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the descent
+# kernel on the 4096x4096 workload (ncu, one pass); None until taken for the
+# current kernel
+MID_DP_TRAFFIC_BYTES = None
+DESCENT_KERNEL = "dp_task_kernel"
 
 
 def parse_args(argv=None):
@@ -137,12 +139,16 @@ def oracle_rate(inst, seconds, seed=2005):
     ny, nx = h.shape
     rng = np.random.default_rng(seed)
 
+    last = {}
+
     def run(n):
         ids = rng.choice(nx * ny, n, replace=False)
         uv = np.stack([ids % nx, ids // nx], 1).astype(np.float32)
         t0 = time.perf_counter()
-        oracle.shadow(h, g, inst["radius"], elev, az, inst["alpha"], inst["lmax"], uv=uv)
-        return time.perf_counter() - t0
+        res = oracle.shadow(h, g, inst["radius"], elev, az, inst["alpha"], inst["lmax"], uv=uv)
+        dt = time.perf_counter() - t0
+        last.update(ids=ids, out=res)
+        return dt
 
     # calibrate on growing samples until one takes >= 1/8 of the target
     n, t = 1024, run(1024)
@@ -155,7 +161,46 @@ def oracle_rate(inst, seconds, seed=2005):
     cores = oracle.num_threads()
     sample = (f"{n} seeded random rays of the {nx}x{ny} tile (every one of the "
               f"{int(inst['lmax'] / (0.5 * g))} samples per ray evaluated in FP64)")
-    return n / t, cores, sample, n, t
+    return n / t, cores, sample, n, t, last
+
+
+def parity_vs_oracle(inst, light, argmin, sampled, n_penumbra=500_000, seed=2006):
+    """The timed step's outputs against the FP64 oracle: on the rays of the CPU
+    baseline's last sample (seeded uniform) plus up to n_penumbra seeded rays
+    among those whose GPU light is in (0, 1) (picked by reading only the GPU
+    light).  Light within 1e-5; an argmin that differs from the oracle's counts
+    as a tie when the oracle's costs at the two samples agree within 1e-6 rad."""
+    import numpy as np
+    import oracle
+    h, g = inst["h"], inst["g"]
+    elev, az = inst["suns"][0]
+    ny, nx = h.shape
+    ids_u = sampled["ids"]
+    lo_u, ao_u, _ = sampled["out"]
+    pen = np.setdiff1d(np.nonzero((light > 0) & (light < 1))[0], ids_u)
+    rng = np.random.default_rng(seed)
+    ids_p = rng.choice(pen, min(n_penumbra, pen.size), replace=False) if pen.size else pen
+    uv_p = np.stack([ids_p % nx, ids_p // nx], 1).astype(np.float32)
+    lo_p, ao_p, _ = oracle.shadow(h, g, inst["radius"], elev, az, inst["alpha"], inst["lmax"],
+                                  uv=uv_p)
+    ids = np.concatenate([ids_u, ids_p])
+    lo = np.concatenate([lo_u, lo_p])
+    ao = np.concatenate([ao_u, ao_p])
+    err = np.abs(light[ids].astype(np.float64) - lo)
+    mism = np.nonzero(argmin[ids] != ao)[0]
+    non_tie = 0
+    for i in mism:
+        r = ids[i]
+        cs = oracle.ray_costs(h, g, inst["radius"], elev, az, inst["lmax"], r % nx, r // nx)
+        jg, jo = int(argmin[r]), int(ao[i])
+        if jg < 1 or jo < 1 or not abs(cs[jg - 1] - cs[jo - 1]) <= 1e-6:
+            non_tie += 1
+    return {"n": int(ids.size), "n_penumbra": int(((lo > 0) & (lo < 1)).sum()),
+            "max_light_err": float(err.max()), "light_tol": 1e-5,
+            "argmin_mismatch": int(mism.size), "argmin_mismatch_non_tie": non_tie,
+            "outputs": "light and argmin of the last timed step",
+            "rays": f"{ids_u.size} seeded uniform rays (the CPU baseline's sample) + "
+                    f"{ids_p.size} seeded rays with GPU light in (0, 1)"}
 
 
 # -------------------------------------------------------------- our arm
@@ -223,6 +268,8 @@ def run_ours(args):
     clocks = sampler.stop()
     if dist is not None:
         dist.barrier()
+    timed_light = light.cpu().numpy()          # the last timed step's outputs (parity)
+    timed_argmin = argmin.cpu().numpy()
     step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
     mip_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     fwd_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
@@ -275,7 +322,7 @@ def run_ours(args):
                and args.block == 0 else None)
     out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                        "frac": achieved / peak, "traffic": traffic,
-                       "kernel": "dp_forward_kernel",
+                       "kernel": DESCENT_KERNEL,
                        "algorithmic_bytes": bytes_fwd,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800",
                        "mean_bound_probes_per_ray": float(cnt[0]) / n_rays,
@@ -447,9 +494,11 @@ def run_ours(args):
         out["polar"] = polar_leg(args, dev, flush)
 
     # ---- CPU oracle on the machine's host cores (bounded sample)
-    rate, cores, sample, n, t = oracle_rate(inst, args.cpu_seconds)
+    rate, cores, sample, n, t, last = oracle_rate(inst, args.cpu_seconds)
     out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                            "sample": sample, "seconds": t}
+    # ---- parity of the timed step's outputs with the oracle (>= 10^6 rays)
+    out["parity"] = parity_vs_oracle(inst, timed_light, timed_argmin, last)
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -566,7 +615,7 @@ def run_reference(args):
     inst = make_instance(CONFIG)
     ny, nx = inst["h"].shape
     # each step: a fixed seeded sample of the workload's rays, about 3 s of CPU work
-    _, cores, _, n, t = oracle_rate(inst, 3.0, seed=1)
+    _, cores, _, n, t, _ = oracle_rate(inst, 3.0, seed=1)
     h, g = inst["h"], inst["g"]
     elev, az = inst["suns"][0]
     rng = np.random.default_rng(7)

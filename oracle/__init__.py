@@ -19,10 +19,10 @@ Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, Monte-Carlo disc area, brute-force block maxima, finite
 differences, and the C-vs-NumPy cross-check); none is "parity unpinned".
 """
-from .cref import (build_oracle, disc_light, shadow, shadow_svec, sun_vector, ray_costs,
-                   sin_elev, grad, maxmip, num_threads, library_path, view_hits, greedy,
-                   shade)
+from .cref import (build_oracle, disc_light, shadow, shadow_svec, sun_vector, sample_uv,
+                   ray_costs, sin_elev, grad, maxmip, num_threads, library_path, view_hits,
+                   greedy, shade)
 
-__all__ = ["build_oracle", "disc_light", "shadow", "shadow_svec", "sun_vector", "ray_costs",
-           "sin_elev", "grad",
+__all__ = ["build_oracle", "disc_light", "shadow", "shadow_svec", "sun_vector", "sample_uv",
+           "ray_costs", "sin_elev", "grad",
            "maxmip", "num_threads", "library_path", "view_hits", "greedy", "shade"]

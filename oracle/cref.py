@@ -63,6 +63,9 @@ def _load():
             lib.or_shadow_svec.restype = None
             lib.or_shadow_svec.argtypes = [p, i32, i32, i64, d, d, i32, p, d, d, d, i32, i64,
                                            p, p, p, p, p, p]
+            lib.or_sample_uv.restype = None
+            lib.or_sample_uv.argtypes = [p, i32, i32, i64, d, d, i32, p, d, i32, i64, p, p, p,
+                                         p]
             lib.or_sun_vector.restype = None
             lib.or_sun_vector.argtypes = [d, d, p]
             lib.or_grad.restype = None
@@ -160,6 +163,23 @@ def shadow_svec(h, g, radius, svec, alpha, lmax, step_texels=0.5, proj="gnomonic
                        float(alpha), float(lmax), float(step_texels), mode, n, _ptr(uv),
                        _ptr(lift), _ptr(light), _ptr(argmin), _ptr(cost), _ptr(cost2))
     return light, argmin, cost, cost2
+
+
+def sample_uv(h, g, radius, svec, j, step_texels=0.5, proj="gnomonic", uv=None, lift=None):
+    """Texel coordinates [n, 2] of the image of sample j[r] of every ray (NaN
+    where j[r] < 1); the light direction as a 3-vector as in ``shadow_svec``."""
+    lib = _load()
+    h64 = _heights(h)
+    ny, nx = h64.shape
+    mode, n, uv, lift = _rays(uv, lift)
+    nr = nx * ny if mode == 0 else n
+    jj = np.ascontiguousarray(j, dtype=np.int64).reshape(-1)
+    assert jj.size == nr
+    sv = np.ascontiguousarray(svec, dtype=np.float64).reshape(3)
+    out = np.empty((nr, 2), np.float64)
+    lib.or_sample_uv(_ptr(h64), nx, ny, nx, float(g), float(radius), PROJ[proj], _ptr(sv),
+                     float(step_texels), mode, n, _ptr(uv), _ptr(lift), _ptr(jj), _ptr(out))
+    return out
 
 
 def ray_costs(h, g, radius, elev, az, lmax, u, v, lift=0.0, step_texels=0.5,

@@ -111,6 +111,30 @@ def shadow(h, g, radius, elev, az, alpha, lmax, step_texels=0.5, proj="gnomonic"
     return light, argmin, cost
 
 
+def sample_uv(h, g, radius, svec, j, step_texels=0.5, proj="gnomonic", uv=None, lift=None):
+    """Texel coordinates [n, 2] of the image of sample j[r] of each ray (NaN where
+    j[r] < 1), like ``oracle.cref.sample_uv``."""
+    h = np.asarray(h, np.float64)
+    ny, nx = h.shape
+    if uv is None:
+        vv, uu = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64),
+                             indexing="ij")
+        uv = np.stack([uu.ravel(), vv.ravel()], axis=1)
+        lift = np.zeros(uv.shape[0])
+    else:
+        uv = np.asarray(uv, np.float32).astype(np.float64).reshape(-1, 2)
+        lift = np.zeros(uv.shape[0]) if lift is None else np.asarray(lift, np.float32).astype(np.float64)
+    j = np.asarray(j, np.int64).reshape(-1)
+    nr = _unit_dir(uv[:, 0], uv[:, 1], nx, ny, g, radius, proj)
+    hp = _bilerp(h, uv[:, 0], uv[:, 1]) + lift
+    p = (radius + hp)[:, None] * nr
+    t = j.astype(np.float64) * step_texels * g
+    q = p + t[:, None] * np.asarray(svec, np.float64)[None, :]
+    us, vs, ok = _to_texel(q, nx, ny, g, radius, proj)
+    ok &= j >= 1
+    return np.stack([np.where(ok, us, np.nan), np.where(ok, vs, np.nan)], axis=1)
+
+
 def maxmip(h):
     """Levels [h, ...] built by padding odd sizes with -inf and reshaping 2x2 blocks."""
     lv = [np.asarray(h, np.float32)]

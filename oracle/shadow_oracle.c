@@ -327,6 +327,34 @@ int64_t or_ray_costs(const double* h, int32_t nx, int32_t ny, int64_t pitch, dou
     return J;
 }
 
+/* Texel coordinates (u, v) of the image of sample j[r] of every ray, with the
+ * light direction given as a 3-vector (as or_shadow_svec): out_uv[2r],
+ * out_uv[2r+1]; NaN when j[r] < 1 or the point has no image.  Lets a caller
+ * find the bilinear cell (and so the texels) a ray's argmin sample reads. */
+void or_sample_uv(const double* h, int32_t nx, int32_t ny, int64_t pitch, double g, double R,
+                  int32_t proj, const double* svec, double step_texels, int32_t mode, int64_t n,
+                  const float* uv, const float* lift, const int64_t* j, double* out_uv) {
+    or_tile t = { h, nx, ny, pitch, g, R, proj };
+    const double s[3] = { svec[0], svec[1], svec[2] };
+    const double delta = step_texels * g;
+    int64_t nr = (mode == 0) ? (int64_t)nx * ny : n;
+    for (int64_t r = 0; r < nr; ++r) {
+        out_uv[2 * r] = out_uv[2 * r + 1] = NAN;
+        if (j[r] < 1) continue;
+        double u, v, l;
+        ray_origin_coords(&t, mode, r, uv, lift, &u, &v, &l);
+        or_origin o;
+        make_origin(&t, u, v, l, &o);
+        const double tj = (double)j[r] * delta;
+        const double q[3] = { o.p[0] + tj * s[0], o.p[1] + tj * s[1], o.p[2] + tj * s[2] };
+        double uq, vq;
+        if (point_to_texel(&t, q, &uq, &vq)) {
+            out_uv[2 * r] = uq;
+            out_uv[2 * r + 1] = vq;
+        }
+    }
+}
+
 /* per-ray radial sine of the sun elevation, n_p . s */
 void or_sin_elev(const double* h, int32_t nx, int32_t ny, int64_t pitch, double g, double R,
                  int32_t proj, double elev, double az, int32_t mode, int64_t n,

@@ -58,6 +58,66 @@ def compare_to_oracle(h, g, R, sun, lmax, step, light, argmin, cost, ray_ids=Non
     return stats
 
 
+# Gradient bars.  The GPU backward evaluates each ray's contributions in FP64
+# (the same formulas as the oracle's analytic gradient) and accumulates them
+# into float32 texels with atomic adds: a texel receiving cnt terms whose
+# absolute values sum to A is off by at most (cnt + 1) 2^-24 A (each term
+# rounded to float32 once, each partial sum once).  On top of that: 1e-6 A
+# for the FP64 differences between the two sides (the GPU works in a local
+# frame, the oracle computes |q| - R plainly: ~1e-10 m over t >= 5 m of cost,
+# amplified near |d| = 1 by F''(d)/F'(d)), and GRAD_REL_TOL |g| per texel.
+GRAD_REL_TOL = 1e-4
+F32_UNIT = 2.0 ** -24
+SAT_MARGIN = 1e-6
+
+
+def grad_weights_mask(light_o, cost_o, sinp_o, alpha, argmin_gpu, argmin_o):
+    """Rays that keep their dL/dlight in gradient comparisons: the GPU and the
+    oracle agree on the argmin (at ties the two subgradients differ), and the
+    oracle's |d| is not within SAT_MARGIN of 1 (there the two sides may
+    disagree on whether the light is saturated, with a contribution of order
+    sqrt(1 - |d|) either way)."""
+    d = np.asarray(cost_o) * np.sqrt(np.maximum(0.0, 1.0 - np.asarray(sinp_o) ** 2)) / alpha
+    near_sat = np.abs(np.abs(d) - 1.0) < SAT_MARGIN
+    return (np.asarray(argmin_gpu) == np.asarray(argmin_o)) & ~near_sat
+
+
+def assert_grad_close(gpu, ref, ref_abs, ref_cnt, rel=GRAD_REL_TOL, what="grad_h"):
+    """Texel by texel: |gpu - ref| <= rel |ref| + ((cnt + 1) 2^-24 + 1e-6) A,
+    with A (ref_abs) and cnt (ref_cnt) the oracle's per-texel sum of
+    |contribution| and number of contributions; texels no ray contributes to
+    must be exactly zero.  Returns statistics."""
+    gpu = np.asarray(gpu, np.float64)
+    err = np.abs(gpu - ref)
+    bar = rel * np.abs(ref) + ((ref_cnt + 1.0) * F32_UNIT + 1e-6) * ref_abs
+    bad = np.argwhere(err > bar)
+    if bad.size:
+        y, x = bad[0]
+        raise AssertionError(
+            f"{what}: {len(bad)} texels beyond the per-texel bar; first ({y},{x}): gpu "
+            f"{gpu[y, x]!r} oracle {ref[y, x]!r} |err| {err[y, x]:.3e} bar {bar[y, x]:.3e} "
+            f"(cnt {ref_cnt[y, x]:.0f}, abs {ref_abs[y, x]:.3e})")
+    nz = ref_cnt > 0
+    return dict(texels=int(nz.sum()), max_rel_err=float((err[nz] / np.maximum(
+        np.abs(ref[nz]), 1e-300)).max()) if nz.any() else 0.0,
+        max_err_over_bar=float((err[nz] / bar[nz]).max()) if nz.any() else 0.0)
+
+
+def stratified_ids(light_gpu, n_uniform, n_penumbra, seed):
+    """Ray ids for full-size parity: n_uniform seeded uniform ids plus up to
+    n_penumbra seeded ids among the rays whose GPU light is in (0, 1) (the
+    penumbra is a few percent of the rays and is where light errors can
+    show).  Only the GPU's light is read, to pick the sample; every value
+    compared comes from the oracle.  Sorted, distinct."""
+    light_gpu = np.asarray(light_gpu)
+    rng = np.random.default_rng(seed)
+    n = light_gpu.size
+    a = rng.choice(n, min(n_uniform, n), replace=False)
+    pen = np.nonzero((light_gpu > 0) & (light_gpu < 1))[0]
+    b = rng.choice(pen, min(n_penumbra, pen.size), replace=False) if pen.size else pen
+    return np.union1d(a, b)
+
+
 def random_ids(n_total, n, seed):
     """n distinct seeded ray ids (independent of any GPU output)."""
     rng = np.random.default_rng(seed)

@@ -14,7 +14,8 @@ import oracle
 from workloads import make_instance, lunar_tile, random_origins, MOON_RADIUS_M
 
 import paper_2005_06671_gb300 as ss
-from _parity import compare_to_oracle, random_ids, LIGHT_TOL
+from _parity import (compare_to_oracle, random_ids, LIGHT_TOL, grad_weights_mask,
+                     assert_grad_close)
 
 pytestmark = pytest.mark.gpu
 R = MOON_RADIUS_M
@@ -154,6 +155,40 @@ def test_seeded_strips_do_not_change_results(strip, tile_w, rpt, sw):
     assert torch.equal(a["cost"].view(torch.int32), b["cost"].view(torch.int32))
 
 
+@pytest.mark.parametrize("name,n,kw", [
+    ("tiny", None, dict()), ("diff", 384, dict()), ("mid", 600, dict()),
+    ("diff", 333, dict(leaf_level=0)), ("diff", 257, dict(refill_min=1)),
+    ("diff", 300, dict(refill_min=32, rays_per_thread=7, ray_tile_w=32)),
+    ("tiny", 190, dict(block_threads=96, rays_per_thread=3, ray_tile_w=16)),
+    ("diff", 200, dict(block_threads=64, seed_width=1, rays_per_thread=64, ray_tile_w=512)),
+    ("tiny", 150, dict(count_samples=True)),
+])
+def test_task_descent_equals_lane_descent_and_uniform(name, n, kw):
+    """The default descent for grid rays on gnomonic tiles (leaf samples as
+    warp-wide tasks) against the single-lane walk (SS_FLAG_LANE_LEAVES) and
+    uniform stepping, bit for bit, over launch shapes: leaf blocks of 2 and 4
+    samples, eager and lazy refills, partial warps, narrow and wide ray
+    rectangles, ragged tile edges."""
+    inst = make_instance(name, n=n)
+    h, g = inst["h"], inst["g"]
+    hf = ss.Heightfield(_dev(h), g, R)
+    mip = ss.ss_build_maxmip(hf)
+    for (elev, az) in inst["suns"][:2]:
+        sun = ss.Sun(elev, az, inst["alpha"])
+        a = ss.ss_shadow_forward(hf, mip, sun, inst["lmax"], **kw)
+        b = ss.ss_shadow_forward(hf, mip, sun, inst["lmax"], lane_leaves=True, **kw)
+        u = ss.ss_shadow_uniform(hf, mip, sun, inst["lmax"])
+        torch.cuda.synchronize()
+        for x in (b, u):
+            assert torch.equal(a["argmin"], x["argmin"])
+            assert torch.equal(a["cost"].view(torch.int32), x["cost"].view(torch.int32))
+            assert torch.equal(a["light"].view(torch.int32), x["light"].view(torch.int32))
+        if kw.get("count_samples"):
+            ca, cb = a["counters"].sum(0).cpu().numpy(), b["counters"].sum(0).cpu().numpy()
+            assert ca[0] > 0 and ca[1] > 0 and cb[0] > 0
+            assert (a["counters"][:, 1] >= 1).float().mean() > 0.9
+
+
 # ------------------------------------------------------------- list mode
 @pytest.mark.parametrize("method", ["dp", "uniform"])
 def test_list_mode_with_lift_vs_oracle(method):
@@ -283,18 +318,17 @@ def test_backward_vs_oracle_gradient(k_sun, pass_cost):
     res = ss.ss_shadow_forward(hf, mip, s, lmax)
     am_gpu = res["argmin"].cpu().numpy().astype(np.int64)
     ol, oa, oc = oracle.shadow(h, g, R, sun[0], sun[1], sun[2], lmax)
+    sinp = oracle.sin_elev(h, g, R, sun[0], sun[1])
     gl = np.random.default_rng(3 + k_sun).normal(size=h.size)
-    gl[am_gpu != oa] = 0.0          # tie rays: the two argmins give different subgradients
+    gl[~grad_weights_mask(ol, oc, sinp, sun[2], am_gpu, oa)] = 0.0
     gh_gpu, gs_gpu = ss.ss_shadow_backward(hf, s, lmax, res["argmin"],
                                            torch.from_numpy(gl.astype(np.float32)).cuda(),
                                            cost=res["cost"] if pass_cost else None)
     torch.cuda.synchronize()
-    gh_o, gs_o = oracle.grad(h, g, R, sun[0], sun[1], sun[2], oa,
-                             gl.astype(np.float32).astype(np.float64))
-    gh_gpu = gh_gpu.cpu().numpy().astype(np.float64)
-    scale = np.abs(gh_o).max()
-    assert scale > 0
-    assert np.abs(gh_gpu - gh_o).max() <= 1e-4 * scale
+    gh_o, gs_o, ah, ch = oracle.grad(h, g, R, sun[0], sun[1], sun[2], oa,
+                                     gl.astype(np.float32).astype(np.float64), with_abs=True)
+    st = assert_grad_close(gh_gpu.cpu().numpy(), gh_o, ah, ch)
+    assert st["texels"] > 50
     np.testing.assert_allclose(gs_gpu.cpu().numpy(), gs_o, rtol=1e-4, atol=1e-6 * np.abs(gs_o).max())
 
 
@@ -306,12 +340,31 @@ def test_autograd_function_matches_oracle():
     light = ss.shadow(ht, ang, g, R, sun[2], lmax)
     loss = ((light - target) ** 2).mean()
     gh, gang = torch.autograd.grad(loss, [ht, ang])
+    # dLoss/dlight as the GPU computed it (float32 light minus target, times 2/n)
+    gl = (2.0 * (light.detach() - target) / h.size).cpu().numpy().astype(np.float64)
+    hf = ss.Heightfield(_dev(h), g, R)
+    fw = ss.ss_shadow_forward(hf, ss.ss_build_maxmip(hf), ss.Sun(*sun), lmax)
+    am_gpu = fw["argmin"].cpu().numpy().astype(np.int64)
+    assert np.array_equal(fw["light"].cpu().numpy(), light.detach().cpu().numpy())
+    # every ray carries weight in the loss, so the GPU's subgradient is taken at
+    # its own argmin, and where that differs from the oracle's the oracle's
+    # gradient is evaluated at the GPU's argmin.  This 80 x 80 crop of the
+    # +-1.5 km generator is far steeper than any config (adjacent texels differ
+    # by up to ~200 m), so near the origin the float32 leaf cost carries up to
+    # 2^-22 |dh| / t ~ 4e-6 rad of rounding (dh ~ 100 m, t = 5 m): a float32
+    # argmin may then differ from the FP64 one by more than the 1e-6 tie bar
+    # of the configs; the two samples' oracle costs must agree within that
+    # rounding bound.
     ol, oa, oc = oracle.shadow(h, g, R, sun[0], sun[1], sun[2], lmax)
-    gl = 2.0 * (light.detach().cpu().numpy().astype(np.float64) - target.cpu().numpy()) / h.size
-    gh_o, gs_o = oracle.grad(h, g, R, sun[0], sun[1], sun[2], oa, gl)
+    for r in np.nonzero(am_gpu != oa)[0]:
+        cs = oracle.ray_costs(h, g, R, sun[0], sun[1], lmax, r % h.shape[1], r // h.shape[1])
+        assert abs(cs[am_gpu[r] - 1] - cs[oa[r] - 1]) <= 4e-6, r
+    sinp = oracle.sin_elev(h, g, R, sun[0], sun[1])
+    assert grad_weights_mask(ol, oc, sinp, sun[2], oa, oa).all()   # no ray at saturation
+    gh_o, gs_o, ah, ch = oracle.grad(h, g, R, sun[0], sun[1], sun[2], am_gpu, gl, with_abs=True)
     assert np.abs(light.detach().cpu().numpy() - ol).max() <= LIGHT_TOL
-    scale = np.abs(gh_o).max()
-    assert np.abs(gh.cpu().numpy() - gh_o).max() <= 1e-4 * scale
+    st = assert_grad_close(gh.cpu().numpy(), gh_o, ah, ch)
+    assert st["texels"] > 20
     np.testing.assert_allclose(gang.numpy(), gs_o[:2], rtol=1e-4, atol=1e-7)
 
 

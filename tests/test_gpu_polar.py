@@ -20,7 +20,7 @@ import oracle
 from workloads import make_instance, lunar_tile, random_origins, MOON_RADIUS_M
 
 import paper_2005_06671_gb300 as ss
-from _parity import compare_to_oracle, random_ids
+from _parity import compare_to_oracle, random_ids, grad_weights_mask, assert_grad_close
 
 pytestmark = pytest.mark.gpu
 R = MOON_RADIUS_M
@@ -130,17 +130,17 @@ def test_polar_backward_vs_oracle_gradient():
     am_gpu = res["argmin"].cpu().numpy().astype(np.int64)
     ol, oa, oc = oracle.shadow(h, g, R, sun[0], sun[1], sun[2], lmax, proj=PROJ)
     assert np.sum((ol > 0) & (ol < 1)) > 100
+    sinp = oracle.sin_elev(h, g, R, sun[0], sun[1], proj=PROJ)
     gl = np.random.default_rng(8).normal(size=h.size)
-    gl[am_gpu != oa] = 0.0
+    gl[~grad_weights_mask(ol, oc, sinp, sun[2], am_gpu, oa)] = 0.0
     gh_gpu, gs_gpu = ss.ss_shadow_backward(hf, s, lmax, res["argmin"],
                                            torch.from_numpy(gl.astype(np.float32)).cuda(),
                                            cost=res["cost"])
     torch.cuda.synchronize()
-    gh_o, gs_o = oracle.grad(h, g, R, sun[0], sun[1], sun[2], oa,
-                             gl.astype(np.float32).astype(np.float64), proj=PROJ)
-    gh_gpu = gh_gpu.cpu().numpy().astype(np.float64)
-    scale = np.abs(gh_o).max()
-    assert scale > 0
-    assert np.abs(gh_gpu - gh_o).max() <= 1e-4 * scale
+    gh_o, gs_o, ah, ch = oracle.grad(h, g, R, sun[0], sun[1], sun[2], oa,
+                                     gl.astype(np.float32).astype(np.float64), proj=PROJ,
+                                     with_abs=True)
+    st = assert_grad_close(gh_gpu.cpu().numpy(), gh_o, ah, ch)
+    assert st["texels"] > 100
     np.testing.assert_allclose(gs_gpu.cpu().numpy(), gs_o, rtol=1e-4,
                                atol=1e-6 * np.abs(gs_o).max())

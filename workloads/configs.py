@@ -44,7 +44,24 @@ def _cache_dir():
     return d
 
 
+# The last few generated tiles, kept in memory (the 16384^2 polar tile takes
+# about a minute to generate); callers get copies.
+_MEMO = {}
+_MEMO_MAX = 3
+
+
 def _tile(n, g, seed, amplitude, craters):
+    key = (n, g, seed, amplitude, craters)
+    if key in _MEMO:
+        return _MEMO[key].copy()
+    h = _tile_uncached(n, g, seed, amplitude, craters)
+    if len(_MEMO) >= _MEMO_MAX:
+        _MEMO.pop(next(iter(_MEMO)))
+    _MEMO[key] = h
+    return h.copy()
+
+
+def _tile_uncached(n, g, seed, amplitude, craters):
     cache = _cache_dir()
     path = os.path.join(cache, f"tile_{n}_{g:g}_{seed}_{amplitude:g}_{craters}.npy") if cache else ""
     if path and os.path.exists(path):
