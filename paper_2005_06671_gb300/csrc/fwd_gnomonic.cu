@@ -1,5 +1,6 @@
 // Forward kernels for gnomonic tiles (Sec. 3.2).
 #include "ss_forward.cuh"
+#include "ss_task.cuh"
 
 namespace ss {
 

@@ -35,6 +35,7 @@ namespace ss {
 // next rays of the block pool (one shared-memory atomic per warp).
 __device__ __forceinline__ ChunkRange block_pool(const FwdArgs& a, int32_t* s_next) {
     if (threadIdx.x == 0) *s_next = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) report_nonfinite_heights(a.stats, a.O.status);
     return chunk_range(blockIdx.x, ray_count(a.T, a.R), a.T.nx, a.T.ny, (int32_t)a.rays_per_block,
                        a.R.mode == 0 ? a.tile_w : 0);
 }
@@ -493,10 +494,30 @@ static cudaError_t dispatch(const FwdArgs& a, int block, cudaStream_t s) {
 }
 #undef SS_FWD_CASE
 
+// defined in ss_task.cuh (included by the gnomonic translation unit only)
+template <bool kCount, bool kPoly>
+__global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_task_kernel(const FwdArgs a);
+
+// The task descent (ss_task.cuh) serves grid rays on gnomonic tiles drawn with
+// column seeds over rectangles, leaf blocks of 2 or 4 samples.
+inline bool use_task_descent(const FwdArgs& a, bool grid, bool stereo, bool light) {
+    return grid && !stereo && !light && a.colseed && a.tile_w > 0 && a.kleaf <= 1 &&
+           !(a.flags & 0x10u);   // SS_FLAG_LANE_LEAVES
+}
+
 template <bool C, bool G, bool P, bool L, bool S>
 struct DpLaunch {
     static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
-        if (L)
+        bool done = false;
+        if constexpr (G && !S && !L) {
+            if (use_task_descent(a, G, S, L)) {
+                dp_task_kernel<C, P><<<grid, block, 0, s>>>(a);
+                done = true;
+            }
+        }
+        if (done)
+            ;
+        else if (L)
             dp_light_kernel<C, G, P, S><<<grid, block, 0, s>>>(a);
         else
             dp_forward_kernel<C, G, P, S><<<grid, block, 0, s>>>(a);
