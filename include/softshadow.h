@@ -39,7 +39,22 @@
  *
  * Memory.  Every pointer named "device" is CUDA device memory owned by the
  * caller; the library never allocates device memory.  Heights are float32,
- * row-major, row stride pitch (elements).  Inputs must be finite.
+ * row-major, row stride pitch (elements).
+ *
+ * Non-finite inputs.  Heights, listed ray origins and lifts, and dL/dlight
+ * should be finite.  A call never faults on non-finite ones (every texel index
+ * is clamped to the tile), and reports them in the caller's device status word
+ * when one is given (ss_outputs.status, the status argument of
+ * ss_shadow_backward_ws): the word is OR-ed with SS_DEV_* bits, read it after
+ * the stream has synchronised (zero it before the call).  Outputs: a ray
+ * whose origin or lift is NaN has no usable sample (light 1, argmin -1); a
+ * sample whose bilinear cell holds a NaN height has a NaN cost and is skipped,
+ * as in the plain definition in IEEE arithmetic (NaN never compares below the
+ * running minimum; maximum-mipmap levels ignore NaN texels).  Rays that read
+ * an infinite height or start at an infinite origin get an unspecified light
+ * in [0, 1] and argmin.  The non-finite height count comes from the
+ * maximum-mipmap build of the same heights (its stats block), so it is
+ * reported by the calls that take that mipmap.
  *
  * Streams.  Every call that takes an ss_stream_t enqueues its work on that
  * stream (NULL = the legacy default stream) and returns without synchronising.
@@ -87,6 +102,20 @@ enum { SS_RAYS_GRID = 0, SS_RAYS_LIST = 1 };
  * reports argmin -1, cost +inf; a ray in umbra reports the first sample found
  * with cost <= -c_sat (a witness, not necessarily the minimum). */
 #define SS_FLAG_LIGHT_ONLY 0x4u
+
+/* ss_shadow_backward_ws: deterministic accumulation (see there). */
+#define SS_FLAG_DETERMINISTIC_BWD 0x8u
+/* ss_shadow_forward, grid rays on gnomonic tiles: by default a warp evaluates
+ * the leaf samples its lanes' walks cannot prune as shared tasks, 32 at a time
+ * (the walks themselves only bound blocks); with this flag each lane evaluates
+ * its own ray's leaf samples inside its walk.  Same results bit for bit. */
+#define SS_FLAG_LANE_LEAVES 0x10u
+
+/* Bits of the device status word (ss_outputs.status, ss_shadow_backward_ws). */
+#define SS_DEV_NONFINITE_HEIGHT 0x1u /* the heights hold a NaN or an infinity      */
+#define SS_DEV_NONFINITE_RAY 0x2u    /* a listed origin or lift is NaN or infinite  */
+#define SS_DEV_NONFINITE_GRAD 0x4u   /* a dL/dlight value is NaN or infinite (that
+                                        ray contributes nothing)                    */
 
 /* Largest supported tile edge and ray length (samples): sample indices and
  * texel coordinates are exact in float32 below these bounds. */
@@ -178,6 +207,8 @@ typedef struct {
     float* cost;           /* optional: c* in rad (+inf when j* = -1), or NULL */
     int32_t* counters;     /* optional [n][2]: (bound probes, leaf samples)
                               when SS_FLAG_COUNT_SAMPLES is set, or NULL       */
+    uint32_t* status;      /* optional device word OR-ed with SS_DEV_* bits
+                              (non-finite heights or ray inputs), or NULL      */
 } ss_outputs;
 
 /* ---------------------------------------------------------------- general */
@@ -192,8 +223,9 @@ const char* ss_version(void);
  * level l below it; levels continue down to 1x1.  The library stores levels
  * 1..L-1 in one caller-allocated device buffer: level l starts at element
  * offset_elems (256-byte aligned) and has row stride pitch (a multiple of 4
- * elements).  Two float32 scalars follow the levels: [stats] = (global max,
- * global min) of the heightfield. */
+ * elements).  Three 32-bit words follow the levels: [stats] = (global max,
+ * global min) of the heightfield as float32 (NaN texels ignored), and the
+ * number of non-finite texels as a uint32. */
 int32_t ss_maxmip_levels(int32_t nx, int32_t ny);          /* L, or 0 on bad size */
 size_t ss_maxmip_bytes(int32_t nx, int32_t ny);            /* 0 on bad size       */
 ss_status ss_maxmip_level_info(int32_t nx, int32_t ny, int32_t level, int32_t* width,
@@ -234,11 +266,42 @@ ss_status ss_shadow_uniform(const ss_heightfield* hf, const float* mip, const ss
  * accumulated: (dL/d elevation, dL/d azimuth, dL/ds_x, dL/ds_y, dL/ds_z), s a
  * free 3-vector.  Rays with j* = -1 or saturated light contribute nothing.
  * Atomic accumulation: summation order, and so the last bits, may vary
- * between runs. */
+ * between runs (float32 atomics on grad_h, FP64 on grad_sun).
+ * params->flags must not hold SS_FLAG_DETERMINISTIC_BWD (use
+ * ss_shadow_backward_ws). */
 ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, const ss_sun* sun,
                              const ss_params* params, const int32_t* argmin, const float* cost,
                              const float* grad_light, float* grad_h, double* grad_sun,
                              ss_stream_t stream);
+
+/* ss_shadow_backward with a caller workspace, a status word and, with
+ * SS_FLAG_DETERMINISTIC_BWD in params->flags, results that are the same bits
+ * on every run and every launch shape (no counterpart in the paper; it makes
+ * a training loop over heights reproducible).  Deterministic mode, two passes
+ * over the rays that need FP64 work:
+ *   1. each contribution to a texel counts into that texel (integer atomics)
+ *      and the largest |contribution| and the largest count are kept;
+ *   2. a power-of-two scale 2^S with (largest |contribution|) (largest count)
+ *      2^S < 2^62 is chosen, every contribution is rounded to the integer
+ *      nearest its value times 2^S and summed in 64-bit integers (exact, so the
+ *      order cannot matter), and grad_h += (float)(sum 2^-S) per texel.
+ *   The sun gradient is summed the same way (scale from the largest |value|
+ *   and the number of rays) and added to grad_sun.
+ *   Error: each texel's sum is exact up to (count) 2^-(S+1) from the
+ *   rounding to integers, far below the float32 rounding of the result.
+ * Without the flag the call behaves as ss_shadow_backward (workspace unused).
+ * workspace: device, at least ss_backward_workspace_bytes(nx, ny, flags)
+ * bytes, 256-byte aligned, not in use by another call in flight.
+ * status: optional device word OR-ed with SS_DEV_NONFINITE_GRAD when a
+ * dL/dlight value is non-finite (that ray is skipped), or NULL.
+ * Errors: as ss_shadow_backward; short or NULL workspace in deterministic
+ * mode -> SS_ERR_OUT_OF_MEMORY / SS_ERR_INVALID_ARG. */
+size_t ss_backward_workspace_bytes(int32_t nx, int32_t ny, uint32_t flags);
+ss_status ss_shadow_backward_ws(const ss_heightfield* hf, const ss_rays* rays, const ss_sun* sun,
+                                const ss_params* params, const int32_t* argmin,
+                                const float* cost, const float* grad_light, float* grad_h,
+                                double* grad_sun, void* workspace, size_t workspace_bytes,
+                                uint32_t* status, ss_stream_t stream);
 
 /* ------------------------------------------------------------- batched
  * Many (heightfield tile, sun) instances of uneven sizes in one persistent

@@ -6,10 +6,11 @@ in-tree by ``paper_2005_06671_gb300.build`` and called through its C ABI
 """
 from .shadow import (Heightfield, Sun, ShadowFn, shadow, ss_build_maxmip, ss_shadow_forward,
                      ss_shadow_uniform, ss_shadow_backward, maxmip_bytes, maxmip_layout,
-                     maxmip_views, maxmip_stats, version, Batch, ss_batch_submit, ss_view_rays,
-                     ss_shadow_greedy, ss_shade)
+                     maxmip_views, maxmip_stats, maxmip_nonfinite_count, version, Batch,
+                     ss_batch_submit, ss_view_rays, ss_shadow_greedy, ss_shade)
 
 __all__ = ["Heightfield", "Sun", "ShadowFn", "shadow", "ss_build_maxmip", "ss_shadow_forward",
            "ss_shadow_uniform", "ss_shadow_backward", "maxmip_bytes", "maxmip_layout",
-           "maxmip_views", "maxmip_stats", "version", "Batch", "ss_batch_submit",
+           "maxmip_views", "maxmip_stats", "maxmip_nonfinite_count", "version", "Batch",
+           "ss_batch_submit",
            "ss_view_rays", "ss_shadow_greedy", "ss_shade"]

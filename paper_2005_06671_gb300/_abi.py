@@ -23,6 +23,11 @@ SS_RAYS_GRID, SS_RAYS_LIST = 0, 1
 SS_FLAG_COUNT_SAMPLES = 0x1
 SS_FLAG_NO_EARLY_EXIT = 0x2
 SS_FLAG_LIGHT_ONLY = 0x4
+SS_FLAG_DETERMINISTIC_BWD = 0x8
+SS_FLAG_LANE_LEAVES = 0x10
+SS_DEV_NONFINITE_HEIGHT = 0x1
+SS_DEV_NONFINITE_RAY = 0x2
+SS_DEV_NONFINITE_GRAD = 0x4
 
 
 class SSHeightfield(ctypes.Structure):
@@ -50,7 +55,8 @@ class SSRays(ctypes.Structure):
 
 
 class SSOutputs(ctypes.Structure):
-    _fields_ = [("light", c_vp), ("argmin", c_vp), ("cost", c_vp), ("counters", c_vp)]
+    _fields_ = [("light", c_vp), ("argmin", c_vp), ("cost", c_vp), ("counters", c_vp),
+                ("status", c_vp)]
 
 
 SSBatchItem._fields_ = [("hf", SSHeightfield), ("mip", c_vp), ("sun", SSSun), ("out", SSOutputs)]
@@ -83,6 +89,10 @@ _SIGNATURES = {
                                   P(SSOutputs), c_vp]),
     "ss_shadow_backward": (c_i32, [P(SSHeightfield), P(SSRays), P(SSSun), P(SSParams), c_vp,
                                    c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "ss_backward_workspace_bytes": (ctypes.c_size_t, [c_i32, c_i32, c_u32]),
+    "ss_shadow_backward_ws": (c_i32, [P(SSHeightfield), P(SSRays), P(SSSun), P(SSParams), c_vp,
+                                      c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp,
+                                      c_vp]),
     "ss_batch_workspace_bytes": (ctypes.c_size_t, [c_i32]),
     "ss_batch_submit": (c_i32, [c_vp, c_i32, P(SSParams), c_vp, ctypes.c_size_t, c_vp]),
     "ss_batch_plan_create": (c_i32, [c_vp, c_i32, P(SSParams), c_vp, ctypes.c_size_t,

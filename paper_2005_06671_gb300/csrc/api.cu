@@ -46,12 +46,20 @@ ss_status check_sun(const ss_sun* sun) {
     return SS_OK;
 }
 
-ss_status check_params(const ss_params* p, double g, int32_t* J, double* delta) {
+constexpr uint32_t kFwdFlags =
+    SS_FLAG_COUNT_SAMPLES | SS_FLAG_NO_EARLY_EXIT | SS_FLAG_LIGHT_ONLY | SS_FLAG_LANE_LEAVES;
+
+static_assert(SS_DEV_NONFINITE_HEIGHT == ss::kDevNonfiniteHeight &&
+                  SS_DEV_NONFINITE_RAY == ss::kDevNonfiniteRay &&
+                  SS_DEV_NONFINITE_GRAD == ss::kDevNonfiniteGrad,
+              "status bits");
+
+ss_status check_params(const ss_params* p, double g, int32_t* J, double* delta,
+                       uint32_t allowed_flags = kFwdFlags) {
     if (!p) return SS_ERR_INVALID_ARG;
     if (!finite_pos(p->max_len_m)) return SS_ERR_INVALID_ARG;
     if (!isfinite(p->step_texels) || p->step_texels < 0.0) return SS_ERR_INVALID_ARG;
-    if (p->flags & ~(SS_FLAG_COUNT_SAMPLES | SS_FLAG_NO_EARLY_EXIT | SS_FLAG_LIGHT_ONLY))
-        return SS_ERR_INVALID_ARG;
+    if (p->flags & ~allowed_flags) return SS_ERR_INVALID_ARG;
     if (p->block_threads != 0 &&
         (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32 != 0))
         return SS_ERR_INVALID_ARG;
@@ -199,9 +207,11 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     a.R.n = n;
     a.R.uv = rays->uv;
     a.R.lift = rays->mode == SS_RAYS_LIST ? rays->lift_m : nullptr;
+    a.R.status = out->status;
     a.O.light = out->light;
     a.O.argmin = out->argmin;
     a.O.cost = out->cost;
+    a.O.status = out->status;
     a.O.counters = (params->flags & SS_FLAG_COUNT_SAMPLES) ? out->counters : nullptr;
     a.stats = mip + L.stats_offset;
     a.kleaf = params->leaf_level >= 0 ? params->leaf_level : (rays->mode == SS_RAYS_GRID ? 1 : 2);
@@ -297,6 +307,7 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
         d.O.argmin = it.out.argmin;
         d.O.cost = it.out.cost;
         d.O.counters = B.count ? it.out.counters : nullptr;
+        d.O.status = it.out.status;
         d.stats = it.mip + B.layouts[i].stats_offset;
         d.n_rays = (int64_t)it.hf.nx * it.hf.ny;
         d.poly = rise_series_ok(&it.hf, &it.sun, J * delta, SS_RAYS_GRID) ? 1 : 0;
@@ -332,6 +343,58 @@ cudaError_t batch_enqueue(const BatchPrep& B, const ss_batch_item* items, int32_
                                     items[i].hf.pitch, items[i].mip, B.layouts[i], s);
     if (e == cudaSuccess) e = ss::launch_batch_forward(B.args, B.block, B.count, s);
     return e;
+}
+
+// ss_shadow_backward / ss_shadow_backward_ws
+ss_status backward_common(const ss_heightfield* hf, const ss_rays* rays, const ss_sun* sun,
+                          const ss_params* params, const int32_t* argmin, const float* cost,
+                          const float* grad_light, float* grad_h, double* grad_sun,
+                          void* workspace, size_t workspace_bytes, uint32_t* status,
+                          bool with_ws, ss_stream_t stream) {
+    ss_status st = check_tile(hf, 2);
+    if (st != SS_OK) return st;
+    if ((st = check_sun(sun)) != SS_OK) return st;
+    int32_t J;
+    double delta;
+    const uint32_t allowed = with_ws ? (kFwdFlags | SS_FLAG_DETERMINISTIC_BWD) : kFwdFlags;
+    if ((st = check_params(params, hf->texel_m, &J, &delta, allowed)) != SS_OK) return st;
+    int64_t n;
+    if ((st = check_rays(rays, hf, &n)) != SS_OK) return st;
+    const bool det = (params->flags & SS_FLAG_DETERMINISTIC_BWD) != 0;
+    if (det) {
+        if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+            return SS_ERR_INVALID_ARG;
+        if (workspace_bytes < ss::backward_det_workspace_bytes(hf->nx, hf->ny))
+            return SS_ERR_OUT_OF_MEMORY;
+    }
+    if (n == 0) return SS_OK;
+    if (!argmin || !grad_light || !grad_h || !grad_sun) return SS_ERR_INVALID_ARG;
+    ss::BwdArgs a{};
+    a.T = make_tile(hf, sun, J, delta);
+    a.R.mode = rays->mode;
+    a.R.n = n;
+    a.R.uv = rays->uv;
+    a.R.lift = rays->mode == SS_RAYS_LIST ? rays->lift_m : nullptr;
+    a.argmin = argmin;
+    a.cost = cost;
+    a.grad_light = grad_light;
+    a.grad_h = grad_h;
+    a.grad_pitch = hf->pitch;
+    a.grad_sun = grad_sun;
+    a.status = status;
+    double e = sun->elevation_rad, az = sun->azimuth_rad;
+    a.ds_de[0] = -sin(e) * sin(az);
+    a.ds_de[1] = -sin(e) * cos(az);
+    a.ds_de[2] = cos(e);
+    a.ds_da[0] = cos(e) * cos(az);
+    a.ds_da[1] = -cos(e) * sin(az);
+    a.ds_da[2] = 0.0;
+    int block = params->block_threads ? params->block_threads : 256;
+    cudaError_t ce = det ? ss::launch_backward_det(a, block, workspace, (cudaStream_t)stream)
+                         : ss::launch_backward(a, block, (cudaStream_t)stream);
+    if (ce != cudaSuccess)
+        return cuda_fail(ce, with_ws ? "ss_shadow_backward_ws" : "ss_shadow_backward");
+    return SS_OK;
 }
 
 }  // namespace
@@ -376,10 +439,10 @@ ss_status ss_maxmip_level_info(int32_t nx, int32_t ny, int32_t level, int32_t* w
     ss::MipLayout L;
     if (!ss::mip_layout(nx, ny, &L)) return SS_ERR_BAD_SIZE;
     if (level < 0 || level > L.levels) return SS_ERR_INVALID_ARG;
-    if (level == L.levels) {   // the stats block
-        if (width) *width = 2;
+    if (level == L.levels) {   // the stats block: max, min, non-finite count
+        if (width) *width = 3;
         if (height) *height = 1;
-        if (pitch) *pitch = 2;
+        if (pitch) *pitch = 3;
         if (offset_elems) *offset_elems = L.stats_offset;
         return SS_OK;
     }
@@ -418,39 +481,23 @@ ss_status ss_shadow_backward(const ss_heightfield* hf, const ss_rays* rays, cons
                              const ss_params* params, const int32_t* argmin, const float* cost,
                              const float* grad_light, float* grad_h, double* grad_sun,
                              ss_stream_t stream) {
-    ss_status st = check_tile(hf, 2);
-    if (st != SS_OK) return st;
-    if ((st = check_sun(sun)) != SS_OK) return st;
-    int32_t J;
-    double delta;
-    if ((st = check_params(params, hf->texel_m, &J, &delta)) != SS_OK) return st;
-    int64_t n;
-    if ((st = check_rays(rays, hf, &n)) != SS_OK) return st;
-    if (n == 0) return SS_OK;
-    if (!argmin || !grad_light || !grad_h || !grad_sun) return SS_ERR_INVALID_ARG;
-    ss::BwdArgs a{};
-    a.T = make_tile(hf, sun, J, delta);
-    a.R.mode = rays->mode;
-    a.R.n = n;
-    a.R.uv = rays->uv;
-    a.R.lift = rays->mode == SS_RAYS_LIST ? rays->lift_m : nullptr;
-    a.argmin = argmin;
-    a.cost = cost;
-    a.grad_light = grad_light;
-    a.grad_h = grad_h;
-    a.grad_pitch = hf->pitch;
-    a.grad_sun = grad_sun;
-    double e = sun->elevation_rad, az = sun->azimuth_rad;
-    a.ds_de[0] = -sin(e) * sin(az);
-    a.ds_de[1] = -sin(e) * cos(az);
-    a.ds_de[2] = cos(e);
-    a.ds_da[0] = cos(e) * cos(az);
-    a.ds_da[1] = -cos(e) * sin(az);
-    a.ds_da[2] = 0.0;
-    int block = params->block_threads ? params->block_threads : 256;
-    cudaError_t ce = ss::launch_backward(a, block, (cudaStream_t)stream);
-    if (ce != cudaSuccess) return cuda_fail(ce, "ss_shadow_backward");
-    return SS_OK;
+    return backward_common(hf, rays, sun, params, argmin, cost, grad_light, grad_h, grad_sun,
+                           nullptr, 0, nullptr, false, stream);
+}
+
+size_t ss_backward_workspace_bytes(int32_t nx, int32_t ny, uint32_t flags) {
+    if (nx < 2 || ny < 2 || nx > SS_MAX_DIM || ny > SS_MAX_DIM) return 0;
+    if (!(flags & SS_FLAG_DETERMINISTIC_BWD)) return 0;
+    return ss::backward_det_workspace_bytes(nx, ny);
+}
+
+ss_status ss_shadow_backward_ws(const ss_heightfield* hf, const ss_rays* rays, const ss_sun* sun,
+                                const ss_params* params, const int32_t* argmin,
+                                const float* cost, const float* grad_light, float* grad_h,
+                                double* grad_sun, void* workspace, size_t workspace_bytes,
+                                uint32_t* status, ss_stream_t stream) {
+    return backward_common(hf, rays, sun, params, argmin, cost, grad_light, grad_h, grad_sun,
+                           workspace, workspace_bytes, status, true, stream);
 }
 
 size_t ss_batch_workspace_bytes(int32_t n_items) {

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
         smem + (size_t)(blockDim.x >> 5) *
                    (sizeof(BatchItemDesc) + sizeof(WarpSched) + 3 * kBatchSeedW * sizeof(int32_t)))
         [threadIdx.x];
-    const Rays grid_rays = { 0, 0, nullptr, nullptr };
+    const Rays grid_rays = { 0, 0, nullptr, nullptr, nullptr };
     if (lane == 0) {
         S.C.cnt = 0;
         S.stash = -1;
@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(256, SS_BATCH_MIN_BLOCKS) batch_dp_kernel(cons
                     if (lane == 0) {
                         S.cur = item;
                         S.span = __ldg(D.stats) - __ldg(D.stats + 1);
+                        report_nonfinite_heights(D.stats, D.O.status);
                     }
                 }
                 __syncwarp();

@@ -29,8 +29,9 @@ struct MipPass {
     float* out[kPassLevels];
     int64_t out_pitch[kPassLevels];
     int32_t out_w[kPassLevels], out_h[kPassLevels];
-    float* stats;                       // (max, min)
-    int32_t write_min;                  // pass 0: fold the tile minimum into stats[1]
+    float* stats;                       // (max, min, non-finite count as uint32)
+    int32_t write_min;                  // pass 0: fold the tile minimum into stats[1] and
+                                        // count its non-finite texels into stats[2]
     int32_t write_max;                  // last pass: store the 1x1 level into stats[0]
 };
 
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(256) mip_pass_kernel(const MipPass a) {
     __shared__ __align__(16) float lv1[32 * 32];
     __shared__ __align__(16) float lv2[16 * 16];
     __shared__ float wmin[8];
+    __shared__ uint32_t wbad[8];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
     const int rp = tid >> 3, cb = tid & 7;
@@ -76,13 +78,21 @@ __global__ void __launch_bounds__(256) mip_pass_kernel(const MipPass a) {
     }
     if (a.write_min) {
         float m = INFINITY;
+        uint32_t bad = 0;   // non-finite texels (fminf/fmaxf skip NaN; infinities count too)
 #pragma unroll
         for (int r = 0; r < 2; ++r)
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-                if (y + r < a.in_h && x + c < a.in_w) m = fminf(m, v[r][c]);
+                if (y + r < a.in_h && x + c < a.in_w) {
+                    m = fminf(m, v[r][c]);
+                    bad += isfinite(v[r][c]) ? 0u : 1u;
+                }
         for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_down_sync(0xffffffffu, m, o));
-        if ((tid & 31) == 0) wmin[tid >> 5] = m;
+        bad = __reduce_add_sync(0xffffffffu, bad);
+        if ((tid & 31) == 0) {
+            wmin[tid >> 5] = m;
+            wbad[tid >> 5] = bad;
+        }
     }
     // level 1 from registers: texels (x0/2 + 4cb + k, y0/2 + rp), k = 0..3
     float4 o1;
@@ -109,8 +119,13 @@ __global__ void __launch_bounds__(256) mip_pass_kernel(const MipPass a) {
     __syncthreads();
     if (a.write_min && tid == 0) {
         float m = wmin[0];
-        for (int w = 1; w < 8; ++w) m = fminf(m, wmin[w]);
+        uint32_t bad = wbad[0];
+        for (int w = 1; w < 8; ++w) {
+            m = fminf(m, wmin[w]);
+            bad += wbad[w];
+        }
         if (m < INFINITY) atomic_min_float(a.stats + 1, m);
+        if (bad) atomicAdd(reinterpret_cast<unsigned int*>(a.stats + 2), bad);
     }
     // levels 2.. (16x16 -> 1x1) through shared memory, sizes known at compile time
     float* src = lv1;
@@ -169,8 +184,10 @@ bool mip_layout(int32_t nx, int32_t ny, MipLayout* L) {
 cudaError_t launch_build_maxmip(const float* h, int32_t nx, int32_t ny, int64_t pitch,
                                 float* mip, const MipLayout& L, cudaStream_t s) {
     float* stats = mip + L.stats_offset;
-    // stats[1] starts at a large positive float (bytes 0x7f7f7f7f = 3.39e38)
+    // stats[1] starts at a large positive float (bytes 0x7f7f7f7f = 3.39e38),
+    // the non-finite count stats[2] at 0
     cudaError_t e = cudaMemsetAsync(stats + 1, 0x7f, sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(stats + 2, 0, sizeof(float), s);
     if (e != cudaSuccess) return e;
     if (L.levels == 1) {
         // 1x1 heightfield: max = min = the single value

@@ -62,6 +62,7 @@ struct Rays {
     int64_t n;
     const float* uv;
     const float* lift;
+    uint32_t* status;          // device status word for non-finite listed inputs, or null
 };
 
 struct Outputs {
@@ -69,7 +70,18 @@ struct Outputs {
     int32_t* argmin;
     float* cost;
     int32_t* counters;
+    uint32_t* status;          // device status word (kDev* bits), or null
 };
+
+// Bits of the device status word (the C ABI's SS_DEV_* values).
+constexpr uint32_t kDevNonfiniteHeight = 0x1u;
+constexpr uint32_t kDevNonfiniteRay = 0x2u;
+constexpr uint32_t kDevNonfiniteGrad = 0x4u;
+
+// Word 2 of a maximum mipmap's stats block: the number of non-finite heights.
+__device__ __forceinline__ void report_nonfinite_heights(const float* stats, uint32_t* status) {
+    if (status && __float_as_uint(__ldg(stats + 2)) != 0u) atomicOr(status, kDevNonfiniteHeight);
+}
 
 // FP64 per-ray geometry (setup, final re-evaluation, backward).
 struct Geom64 {

@@ -51,6 +51,7 @@ struct BwdArgs {
     int64_t grad_pitch;
     double* grad_sun;
     double ds_de[3], ds_da[3];
+    uint32_t* status;           // device status word (non-finite dL/dlight), or null
 };
 
 cudaError_t launch_build_maxmip(const float* h, int32_t nx, int32_t ny, int64_t pitch,
@@ -58,6 +59,8 @@ cudaError_t launch_build_maxmip(const float* h, int32_t nx, int32_t ny, int64_t 
 cudaError_t launch_dp_forward(const FwdArgs& a, int block, cudaStream_t s);
 cudaError_t launch_uniform_forward(const FwdArgs& a, int block, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs& a, int block, cudaStream_t s);
+size_t backward_det_workspace_bytes(int32_t nx, int32_t ny);
+cudaError_t launch_backward_det(const BwdArgs& a, int block, void* workspace, cudaStream_t s);
 
 // camera of the view-ray caster (mirrors ss_camera)
 struct ViewCamera {

@@ -128,6 +128,8 @@ __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t 
         ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
         uf = R.uv[2 * r];
         vf = R.uv[2 * r + 1];
+        if (R.status && !(isfinite(uf) && isfinite(vf) && (!R.lift || isfinite(R.lift[r]))))
+            atomicOr(R.status, kDevNonfiniteRay);
     }
     float se;
     if (!kStereo) {

@@ -95,6 +95,12 @@ def maxmip_stats(mip, nx, ny):
     return mip[o:o + 2]
 
 
+def maxmip_nonfinite_count(mip, nx, ny):
+    """Number of non-finite heights counted by the build (stats word 2), on the host."""
+    w, h, p, o = maxmip_layout(nx, ny)[-1]
+    return int(mip[o + 2:o + 3].view(torch.int32).item())
+
+
 def ss_build_maxmip(hf: Heightfield, mip=None, stream=None):
     ny, nx = hf.shape
     if mip is None:
@@ -139,9 +145,14 @@ def _outputs(n, device, want_cost, count, out):
     counters = out.get("counters")
     if counters is None and count:
         counters = torch.empty((n, 2), dtype=torch.int32, device=device)
+    status = out.get("status")   # optional device int32/uint32 word (SS_DEV_* bits)
+    if status is not None and not (status.is_cuda and status.dtype == torch.int32 and
+                                   status.numel() >= 1):
+        raise ValueError("status must be an int32 CUDA tensor of at least one element")
     c = SSOutputs(light.data_ptr(), argmin.data_ptr(), None if cost is None else cost.data_ptr(),
-                  None if counters is None else counters.data_ptr())
-    return c, dict(light=light, argmin=argmin, cost=cost, counters=counters)
+                  None if counters is None else counters.data_ptr(),
+                  None if status is None else status.data_ptr())
+    return c, dict(light=light, argmin=argmin, cost=cost, counters=counters, status=status)
 
 
 def _forward(fn_name, hf, mip, sun, max_len_m, step_texels, uv, lift, flags, block_threads,
@@ -161,12 +172,17 @@ def _forward(fn_name, hf, mip, sun, max_len_m, step_texels, uv, lift, flags, blo
 def ss_shadow_forward(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5, uv=None,
                       lift=None, count_samples=False, block_threads=0, leaf_level=-1,
                       want_cost=True, out=None, stream=None, rays_per_thread=0, refill_min=0,
-                      ray_tile_w=0, light_only=False, strip_len=0, seed_width=0):
+                      ray_tile_w=0, light_only=False, strip_len=0, seed_width=0,
+                      lane_leaves=False):
     """Exact max-mip descent.  Returns dict(light, argmin, cost, counters).
     light_only: saturation cutoffs (exact light; argmin/cost exact in the penumbra).
     strip_len: rays per seeded strip (0 = default, 1 = no seeding).
-    seed_width: half-width of a seed window (0 = default)."""
-    flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (SS_FLAG_LIGHT_ONLY if light_only else 0)
+    seed_width: half-width of a seed window (0 = default).
+    lane_leaves: leaf samples evaluated by each walking lane instead of as
+    warp-wide tasks (grid rays on gnomonic tiles; same results)."""
+    flags = ((SS_FLAG_COUNT_SAMPLES if count_samples else 0) |
+             (SS_FLAG_LIGHT_ONLY if light_only else 0) |
+             (_abi.SS_FLAG_LANE_LEAVES if lane_leaves else 0))
     return _forward("ss_shadow_forward", hf, mip, sun, max_len_m, step_texels, uv, lift, flags,
                     block_threads, leaf_level, want_cost, out, stream, rays_per_thread,
                     refill_min, ray_tile_w, strip_len, seed_width)
@@ -187,10 +203,13 @@ def ss_shadow_uniform(hf: Heightfield, mip, sun: Sun, max_len_m, step_texels=0.5
 # ---------------------------------------------------------------- backward
 def ss_shadow_backward(hf: Heightfield, sun: Sun, max_len_m, argmin, grad_light, step_texels=0.5,
                        uv=None, lift=None, grad_h=None, grad_sun=None, block_threads=0,
-                       stream=None, cost=None):
+                       stream=None, cost=None, deterministic=False, status=None, workspace=None):
     """Accumulates dL/dh into grad_h [ny, nx] (float32) and dL/d(elev, az, s_x, s_y, s_z)
     into grad_sun (float64 [5]); allocates zeroed ones when not given.  ``cost``
-    (the forward's cost output) lets saturated rays be skipped early."""
+    (the forward's cost output) lets saturated rays be skipped early.
+    ``deterministic``: the same bits on every run (ss_shadow_backward_ws with
+    SS_FLAG_DETERMINISTIC_BWD; ``workspace`` is allocated when not given).
+    ``status``: optional int32 CUDA word OR-ed with SS_DEV_NONFINITE_GRAD."""
     rays, n = _rays(hf, uv, lift)
     if grad_h is None:
         grad_h = torch.zeros_like(hf.h)
@@ -200,13 +219,29 @@ def ss_shadow_backward(hf: Heightfield, sun: Sun, max_len_m, argmin, grad_light,
         grad_sun = torch.zeros(5, dtype=torch.float64, device=hf.h.device)
     argmin = argmin.contiguous()
     grad_light = grad_light.to(torch.float32).contiguous()
-    prm = _params(max_len_m, step_texels, 0, block_threads, -1)
+    flags = _abi.SS_FLAG_DETERMINISTIC_BWD if deterministic else 0
+    prm = _params(max_len_m, step_texels, flags, block_threads, -1)
     cost = None if cost is None else cost.contiguous()
-    check(_abi.lib().ss_shadow_backward(ctypes.byref(hf.c()), ctypes.byref(rays),
-                                        ctypes.byref(sun.c()), ctypes.byref(prm),
-                                        _ptr(argmin), _ptr(cost), _ptr(grad_light), _ptr(grad_h),
-                                        _ptr(grad_sun), _stream_ptr(stream)),
-          "ss_shadow_backward")
+    if not deterministic and status is None:
+        check(_abi.lib().ss_shadow_backward(ctypes.byref(hf.c()), ctypes.byref(rays),
+                                            ctypes.byref(sun.c()), ctypes.byref(prm),
+                                            _ptr(argmin), _ptr(cost), _ptr(grad_light),
+                                            _ptr(grad_h), _ptr(grad_sun), _stream_ptr(stream)),
+              "ss_shadow_backward")
+        return grad_h, grad_sun
+    ny, nx = hf.shape
+    nb = int(_abi.lib().ss_backward_workspace_bytes(nx, ny, flags))
+    if workspace is None and nb > 0:
+        workspace = torch.empty(nb, dtype=torch.uint8, device=hf.h.device)
+    if status is not None and not (status.is_cuda and status.dtype == torch.int32):
+        raise ValueError("status must be an int32 CUDA tensor")
+    check(_abi.lib().ss_shadow_backward_ws(ctypes.byref(hf.c()), ctypes.byref(rays),
+                                           ctypes.byref(sun.c()), ctypes.byref(prm),
+                                           _ptr(argmin), _ptr(cost), _ptr(grad_light),
+                                           _ptr(grad_h), _ptr(grad_sun), _ptr(workspace),
+                                           0 if workspace is None else workspace.numel(),
+                                           _ptr(status), _stream_ptr(stream)),
+          "ss_shadow_backward_ws")
     return grad_h, grad_sun
 
 

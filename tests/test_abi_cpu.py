@@ -72,6 +72,7 @@ def _fwd(hf, sun, prm, rays, out, mip=FAKE):
     (lambda a: setattr(a[2], "max_len_m", 1e9), 2),
     (lambda a: setattr(a[2], "step_texels", -0.5), 1),
     (lambda a: setattr(a[2], "flags", 0x80), 1),
+    (lambda a: setattr(a[2], "flags", 0x8), 1),      # deterministic: a backward flag
     (lambda a: setattr(a[2], "block_threads", 100), 1),
     (lambda a: setattr(a[2], "leaf_level", 40), 1),
     (lambda a: setattr(a[2], "strip_len", -1), 1),
@@ -220,3 +221,30 @@ def test_shade_rejects_bad_lights():
         st = lib.ss_shade(ctypes.byref(hf), ctypes.byref(rays), ctypes.cast(arr, ctypes.c_void_p),
                           n, None, None)
         assert st == expect
+
+
+def test_backward_entry_points_reject_bad_arguments():
+    """ss_shadow_backward refuses the deterministic flag (it has no workspace);
+    ss_shadow_backward_ws needs a large enough, 256-byte aligned workspace for it."""
+    lib = _abi.lib()
+    hf, sun, prm, rays, out = _good()
+    nb = lib.ss_backward_workspace_bytes(64, 64, _abi.SS_FLAG_DETERMINISTIC_BWD)
+    assert nb >= 64 * 64 * 12
+    assert lib.ss_backward_workspace_bytes(64, 64, 0) == 0
+    assert lib.ss_backward_workspace_bytes(1, 64, _abi.SS_FLAG_DETERMINISTIC_BWD) == 0
+    f = ctypes.c_void_p(FAKE)
+
+    def bwd(p, ws=None, nbytes=0):
+        return lib.ss_shadow_backward_ws(ctypes.byref(hf), ctypes.byref(rays), ctypes.byref(sun),
+                                         ctypes.byref(p), f, None, f, f, f,
+                                         None if ws is None else ctypes.c_void_p(ws), nbytes,
+                                         None, None)
+
+    prm.flags = _abi.SS_FLAG_DETERMINISTIC_BWD
+    assert lib.ss_shadow_backward(ctypes.byref(hf), ctypes.byref(rays), ctypes.byref(sun),
+                                  ctypes.byref(prm), f, None, f, f, f, None) == 1
+    assert bwd(prm) == 1                              # no workspace
+    assert bwd(prm, FAKE + 16, nb) == 1               # not 256-byte aligned
+    assert bwd(prm, FAKE, nb - 1) == 3                # too small
+    prm.flags = 0x80
+    assert bwd(prm, FAKE, nb) == 1
