@@ -388,6 +388,42 @@ def test_runner_up_cost_is_second_smallest_sample_cost():
     assert np.all(c2 >= c)
 
 
+@pytest.mark.parametrize("proj", ["gnomonic", "polar_stereo"])
+def test_sample_uv_matches_numpy_and_gradient_cells(proj):
+    """sample_uv (C) against the NumPy restatement, and the texels the analytic
+    gradient writes for a ray lie in the bilinear cell of its argmin sample's
+    image or in the origin's cell."""
+    g, lmax = 20.0, 1500.0
+    h = _fd_case(31, proj)
+    elev, az = math.radians(2.0), math.radians(57.0)
+    s = oracle.sun_vector(elev, az)
+    uv = random_origins(1500, 40, 40, seed=52, margin=1.0)
+    lift = np.random.default_rng(53).uniform(0, 5, 1500).astype(np.float32)
+    light, argmin, cost, _ = oracle.shadow_svec(h, g, R, s, math.radians(8.0), lmax, proj=proj,
+                                                uv=uv, lift=lift)
+    a = oracle.sample_uv(h, g, R, s, argmin, proj=proj, uv=uv, lift=lift)
+    b = mini.sample_uv(h, g, R, s, argmin, proj=proj, uv=uv, lift=lift)
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    fin = np.isfinite(a)
+    assert fin.any()
+    np.testing.assert_allclose(a[fin], b[fin], rtol=0, atol=1e-9)
+    checked = 0
+    for r in np.nonzero((light > 0) & (light < 1) & (argmin > 0))[0][:40]:
+        one = np.zeros(1500)
+        one[r] = 1.0
+        gh, _ = oracle.grad(h, g, R, elev, az, math.radians(8.0), argmin, one, proj=proj, uv=uv,
+                            lift=lift)
+        i0 = min(int(np.floor(a[r, 0])), 38)
+        j0 = min(int(np.floor(a[r, 1])), 38)
+        oi = min(int(np.floor(uv[r, 0])), 38)
+        oj = min(int(np.floor(uv[r, 1])), 38)
+        for (y, x) in np.argwhere(gh != 0):
+            assert (i0 <= x <= i0 + 1 and j0 <= y <= j0 + 1) or (oi <= x <= oi + 1 and
+                                                                  oj <= y <= oj + 1)
+        checked += 1
+    assert checked >= 10
+
+
 def test_grad_abs_and_count_outputs():
     """The per-texel |contribution| sum and count outputs of or_grad: with gL of
     one sign on a single ray, abs equals |grad| texel by texel on the sample
