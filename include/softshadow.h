@@ -50,9 +50,10 @@
  * whose origin or lift is NaN has no usable sample (light 1, argmin -1); a
  * sample whose bilinear cell holds a NaN height has a NaN cost and is skipped,
  * as in the plain definition in IEEE arithmetic (NaN never compares below the
- * running minimum; maximum-mipmap levels ignore NaN texels).  Rays that read
- * an infinite height or start at an infinite origin get an unspecified light
- * in [0, 1] and argmin.  The non-finite height count comes from the
+ * running minimum; maximum-mipmap levels ignore NaN texels).  Rays whose
+ * origin cell holds a NaN (a grid ray takes its own texel's value), that
+ * read an infinite height or start at an infinite origin get an unspecified
+ * light in [0, 1] and argmin.  The non-finite height count comes from the
  * maximum-mipmap build of the same heights (its stats block), so it is
  * reported by the calls that take that mipmap.
  *

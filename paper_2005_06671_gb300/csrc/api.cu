@@ -127,6 +127,9 @@ ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, doubl
     T.sx_f = (float)s[0];
     T.sy_f = (float)s[1];
     T.R_f = (float)hf->radius_m;
+    T.g_f = (float)hf->texel_m;
+    T.cx_f = (float)T.cx;
+    T.cy_f = (float)T.cy;
     T.alpha_f = (float)sun->angular_radius_rad;
     auto split = [](double x, float& hi, float& lo) {
         hi = (float)x;

@@ -52,6 +52,7 @@ struct Tile {
     float sz_f;                // (float)sz
     float alpha_f;
     float sx_f, sy_f, R_f;     // (float)sx, (float)sy, (float)R
+    float g_f, cx_f, cy_f;     // (float)g, (float)cx, (float)cy (converted once, on the host)
     // float-float (hi + lo) copies for the grid-ray setup (df_* below)
     float g_hi, g_lo, R_lo, RR_hi, RR_lo, delta_hi, delta_lo, igR_hi, igR_lo;
     float Rsx_hi, Rsx_lo, Rsy_hi, Rsy_lo, sz_lo, szR_f;
@@ -354,7 +355,9 @@ __device__ __forceinline__ bool exit_fast(const Tile& T, double up, double vp, d
         // the float estimate is within ~3e-7 jf of the crossing: when that
         // leaves no doubt about floor(jf) (or about jf >= J), it is the answer
         const float margin = 1e-6f * fabsf(jf) + 1e-3f;
-        if (den > 0.0f && jf >= 0.0f) {
+        // the image reaches the bound at j = d / den >= 0 when den has the sign
+        // of the slope (of d); otherwise it never does (or den is ~0): exact test
+        if ((a > 0.0f ? den > 0.0f : den < 0.0f) && jf >= 0.0f) {
             if (jf >= (float)T.J + margin) {
                 continue;                            // no exit before J on this axis
             }
@@ -466,7 +469,9 @@ __device__ __forceinline__ bool exit_fast_df(const Tile& T, float u, float v, DF
         const float den = a - b.hi * d;
         const float jf = den != 0.0f ? d / den : INFINITY;
         const float margin = 1e-6f * fabsf(jf) + 1e-3f;
-        if (den > 0.0f && jf >= 0.0f) {
+        // the image reaches the bound at j = d / den >= 0 when den has the sign
+        // of the slope (of d); otherwise it never does (or den is ~0): exact test
+        if ((a > 0.0f ? den > 0.0f : den < 0.0f) && jf >= 0.0f) {
             if (jf >= (float)T.J + margin) continue;
             const float fl = floorf(jf), fr = jf - fl;
             if (fr > margin && fr < 1.0f - margin && jf < (float)T.J) {
@@ -508,8 +513,8 @@ __device__ __forceinline__ void make_rayf_gnomonic_grid(const Tile& T, int32_t u
                                                         float& sin_e) {
     const float uf = (float)u, vf = (float)v;
     const DF g = { T.g_hi, T.g_lo };
-    const DF Xp = df_mul_f(g, __fsub_rn(uf, (float)T.cx));   // u - cx exact (half-integers)
-    const DF Yp = df_mul_f(g, __fsub_rn(vf, (float)T.cy));
+    const DF Xp = df_mul_f(g, __fsub_rn(uf, T.cx_f));   // u - cx exact (half-integers)
+    const DF Yp = df_mul_f(g, __fsub_rn(vf, T.cy_f));
     const DF m2 = df_add(df_add(df_mul(Xp, Xp), df_mul(Yp, Yp)), DF{ T.RR_hi, T.RR_lo });
     const DF rho = df_add(DF{ T.R_f, T.R_lo }, DF{ h, 0.0f });
     const DF f = df_mul(DF{ T.delta_hi, T.delta_lo }, df_div(df_sqrt(m2), rho));
@@ -518,7 +523,7 @@ __device__ __forceinline__ void make_rayf_gnomonic_grid(const Tile& T, int32_t u
     const DF Au = df_mul(k, df_add(DF{ T.Rsx_hi, T.Rsx_lo }, df_neg(df_mul(sz, Xp))));
     const DF Av = df_mul(k, df_add(DF{ T.Rsy_hi, T.Rsy_lo }, df_neg(df_mul(sz, Yp))));
     const DF b = df_mul_f(f, T.szR_f);
-    const float Xf = (uf - (float)T.cx) * (float)T.g, Yf = (vf - (float)T.cy) * (float)T.g;
+    const float Xf = (uf - T.cx_f) * T.g_f, Yf = (vf - T.cy_f) * T.g_f;
     const float imf = rsqrtf(Xf * Xf + Yf * Yf + T.R_f * T.R_f);
     const float se = (Xf * T.sx_f + Yf * T.sy_f + T.R_f * T.sz_f) * imf;
     const float rhof = T.R_f + h;
@@ -577,7 +582,7 @@ __device__ __forceinline__ void make_rayf_gnomonic(const Tile& T, double up, dou
     const double k = f * T.inv_gR;
     const double Au = k * (T.R * T.sx - T.sz * Xp), Av = k * (T.R * T.sy - T.sz * Yp);
     const double b = f * T.sz * T.inv_R;
-    const float Xf = (uf - (float)T.cx) * (float)T.g, Yf = (vf - (float)T.cy) * (float)T.g;
+    const float Xf = (uf - T.cx_f) * T.g_f, Yf = (vf - T.cy_f) * T.g_f;
     const float imf = rsqrtf(Xf * Xf + Yf * Yf + T.R_f * T.R_f);
     const float se = (Xf * T.sx_f + Yf * T.sy_f + T.R_f * T.sz_f) * imf;
     const float rhof = T.R_f + (float)hp;

@@ -494,28 +494,31 @@ static cudaError_t dispatch(const FwdArgs& a, int block, cudaStream_t s) {
 }
 #undef SS_FWD_CASE
 
-// defined in ss_task.cuh (included by the gnomonic translation unit only)
-template <bool kCount, bool kPoly>
+// defined in ss_task.cuh
+template <bool kCount, bool kGrid, bool kPoly, bool kStereo>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_task_kernel(const FwdArgs a);
 
-// The task descent (ss_task.cuh) serves grid rays on gnomonic tiles drawn with
-// column seeds over rectangles, leaf blocks of 2 or 4 samples.
+// The task descent (ss_task.cuh) serves exact walks with column seeds on
+// gnomonic tiles: grid rays in rectangles (leaf blocks of <= 4 samples),
+// listed rays in runs (<= 8).  Stereographic tiles keep the single-lane walk:
+// their FP64 ray setup, run by the few lanes a service refills, outweighs what
+// the tasks save (polar view, 6.0 M rays: 70 ms against 65 ms).
 inline bool use_task_descent(const FwdArgs& a, bool grid, bool stereo, bool light) {
-    return grid && !stereo && !light && a.colseed && a.tile_w > 0 && a.kleaf <= 1 &&
-           !(a.flags & 0x10u);   // SS_FLAG_LANE_LEAVES
+    return !light && !stereo && a.colseed && (!grid || a.tile_w > 0) &&
+           a.kleaf <= (grid ? 1 : 2) && !(a.flags & 0x10u);   // SS_FLAG_LANE_LEAVES
 }
 
 template <bool C, bool G, bool P, bool L, bool S>
 struct DpLaunch {
     static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
-        bool done = false;
-        if constexpr (G && !S && !L) {
+        bool tasks = false;
+        if constexpr (!S && !L) {   // defined for gnomonic tiles only (fwd_gnomonic.cu)
             if (use_task_descent(a, G, S, L)) {
-                dp_task_kernel<C, P><<<grid, block, 0, s>>>(a);
-                done = true;
+                dp_task_kernel<C, G, P, S><<<grid, block, 0, s>>>(a);
+                tasks = true;
             }
         }
-        if (done)
+        if (tasks)
             ;
         else if (L)
             dp_light_kernel<C, G, P, S><<<grid, block, 0, s>>>(a);

@@ -33,16 +33,14 @@ __device__ __forceinline__ float cos_elev_f32(const Tile& T, const Rays& R, int6
         u = R.uv[2 * r];
         v = R.uv[2 * r + 1];
     }
-    const float g = (float)T.g, Rs = (float)T.R;
-    const float X = (u - (float)T.cx) * g, Y = (v - (float)T.cy) * g;
+    const float g = T.g_f, Rs = T.R_f;
+    const float X = (u - T.cx_f) * g, Y = (v - T.cy_f) * g;
     float se;
     if (!stereo) {
-        se = (X * (float)T.sx + Y * (float)T.sy + Rs * (float)T.sz) *
-             rsqrtf(X * X + Y * Y + Rs * Rs);
+        se = (X * T.sx_f + Y * T.sy_f + Rs * T.sz_f) * rsqrtf(X * X + Y * Y + Rs * Rs);
     } else {   // n = (2x, 2y, 1 - x^2 - y^2) / (1 + x^2 + y^2), (x, y) = (X, Y) / 2R
         const float k = 0.5f / Rs, x = X * k, y = Y * k, q = x * x + y * y;
-        se = (2.0f * x * (float)T.sx + 2.0f * y * (float)T.sy + (1.0f - q) * (float)T.sz) /
-             (1.0f + q);
+        se = (2.0f * x * T.sx_f + 2.0f * y * T.sy_f + (1.0f - q) * T.sz_f) / (1.0f + q);
     }
     return sqrtf(fmaxf(0.0f, 1.0f - se * se));
 }

@@ -3,16 +3,19 @@
 // intersected with the displaced terrain, and the maximum mipmap lets a ray
 // skip what it passes above).
 //
-// Per pixel (FP64 throughout; this is setup, not the per-sample hot path):
+// Per pixel:
 //   d = unit(forward + a right + b up), x(tau) = C + tau d, samples tau_k = k step;
 //   the hit is the first sample whose texel image is in the tile and lies on or
-//   below the terrain (|x| - R - h <= 0); when the sample before it is in the
-//   tile too the crossing is refined by 48 bisection halvings.
+//   below the terrain (|x| - R - h <= 0, decided in FP64); when the sample
+//   before it is in the tile too the crossing is refined in FP64 by 48
+//   bisection halvings.
 // Sample blocks are walked near-to-far like the shadow descent (aligned blocks
-// of 2^k samples, next block at s0 += 2^k): a block is skipped when the ray's
-// lowest height over it exceeds the maximum-mipmap value over its texel
-// footprint, or when the footprint misses the tile, so the first sample found
-// below the terrain is the first one overall.
+// of 2^k samples, next block at s0 += 2^k) in float32: a block is skipped when
+// the ray's lowest height over it exceeds the maximum-mipmap value over its
+// texel footprint by more than the float32 rounding, or when the footprint
+// misses the tile; a sample is tested in FP64 unless float32 shows it clearly
+// above the terrain or off the tile.  So the first sample found below the
+// terrain is the first one overall, the same sample as an FP64 march.
 //
 // Then the hits are compacted in pixel order (per-block counts, one scan block,
 // a scatter), so the ray list is deterministic.
@@ -81,6 +84,40 @@ __device__ __forceinline__ float box_max(const Tile& T, const Pyramid& P, int32_
     return fmaxf(fmaxf(a, b), fmaxf(c, e));
 }
 
+// float32 state of one view ray.  The camera is taken relative to the tile
+// centre's point on the sphere, P0 = (0, 0, R) (a few km, so float32 keeps it
+// to a few mm); the ray height over the sphere is the camera altitude plus
+// rise(tau) = |C + tau d| - |C| in the cancellation-free form of the shadow
+// rays (rise_of), so heights carry ~1e-2 m of rounding and texel positions
+// ~2e-3 texel (5 m texels) over the ray's 150 km.
+struct ViewRayF {
+    float cx, cy, cz;        // C - P0
+    float dx, dy, dz;        // unit direction
+    float alt;               // |C| - R
+    float two_r_g;           // 2R/g (stereographic) or R/g (gnomonic)
+    float zsum;              // |C| + R: |x| + x_z = zsum + rise + cz + tau dz
+    RayF rise;               // B = 2 C.d, inv_2rho = 1/(2|C|): rise_of's fields
+};
+
+// texel coordinates of the ray point at tau (rise = rise(tau)); false when the
+// point has no image (gnomonic: not in front of the plane; stereographic: near
+// the antipode)
+__device__ __forceinline__ bool view_image_f(const Tile& T, const ViewRayF& q, float tau,
+                                             float rise, float& u, float& v) {
+    const float x = q.cx + tau * q.dx, y = q.cy + tau * q.dy;
+    float den;
+    if (T.proj == 0) {
+        den = T.R_f + (q.cz + tau * q.dz);              // x_z
+    } else {
+        den = q.zsum + (rise + (q.cz + tau * q.dz));    // |x| + x_z
+    }
+    if (!(den > 1.0f)) return false;
+    const float k = q.two_r_g / den;
+    u = x * k + T.cx_f;
+    v = y * k + T.cy_f;
+    return true;
+}
+
 __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) {
     const int64_t npix = (int64_t)a.cam.W * a.cam.H;
     const int64_t pix = (int64_t)blockIdx.x * kViewBlock + threadIdx.x;
@@ -117,14 +154,36 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
             }
         }
         // image circle of the ray (stereographic): 1/(8 r) in texels^-1
-        double inv8r = 0.0;
+        float inv8r = 0.0f;
         if (T.proj != 0) {
             const double N[3] = { C[1] * d[2] - C[2] * d[1], C[2] * d[0] - C[0] * d[2],
                                   C[0] * d[1] - C[1] * d[0] };
             const double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-            inv8r = nn > 0.0 ? fabs(N[2]) / nn * T.g / (16.0 * T.R) : 0.0;
+            inv8r = nn > 0.0 ? (float)(fabs(N[2]) / nn * T.g / (16.0 * T.R)) : 0.0f;
         }
-        const double tv = -cd;   // closest approach to the centre
+        ViewRayF q;
+        const double cn = sqrt(cc);
+        q.cx = (float)C[0];
+        q.cy = (float)C[1];
+        q.cz = (float)(C[2] - T.R);
+        q.dx = (float)d[0];
+        q.dy = (float)d[1];
+        q.dz = (float)d[2];
+        q.alt = (float)(cn - T.R);
+        q.two_r_g = (float)((T.proj == 0 ? 1.0 : 2.0) * T.R / T.g);
+        q.zsum = (float)(cn + T.R);
+        q.rise.B = (float)(2.0 * cd);
+        q.rise.inv_2rho = (float)(0.5 / cn);
+        const float stepf = (float)a.step;
+        const float tv = (float)(-cd);   // closest approach to the centre
+        // float32 guards: a block is skipped when its lowest ray height is above
+        // the maximum height under its footprint by more than kBlockGuard (the
+        // rounding of the float32 height is ~1e-2 m); a sample is ruled out
+        // when it is above the bilinear terrain by more than kLeafGuard plus a
+        // share of its cell's height range (position error <= 2e-3 texel);
+        // anything closer is decided in FP64 (below()), as before.
+        constexpr float kBlockGuard = 0.05f, kLeafGuard = 0.05f, kPosMargin = 0.01f;
+        const float nxm = (float)(T.nx - 1), nym = (float)(T.ny - 1);
         if (k0 <= k1) {
             const int64_t b0 = k0 - 1, n = k1 - b0;
             int32_t kk = 0;
@@ -137,42 +196,64 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
                 const int64_t jb = min(b0 + s0 + ((int64_t)1 << k), k1);
                 bool descend = false;
                 if (k <= kViewLeaf) {
-                    for (int64_t q = ja; q <= jb; ++q) {
-                        bool ins;
-                        double u, v;
-                        if (below(T, C, d, (double)q * a.step, ins, u, v)) {
-                            hit_k = q;
-                            break;
+                    for (int64_t qj = ja; qj <= jb; ++qj) {
+                        const float t = (float)qj * stepf;
+                        const float rs = rise_of<false>(q.rise, t);
+                        float u, v;
+                        bool decide = true;   // false: certainly no hit at this sample
+                        if (view_image_f(T, q, t, rs, u, v)) {
+                            const bool out = u < -kPosMargin || u > nxm + kPosMargin ||
+                                             v < -kPosMargin || v > nym + kPosMargin;
+                            const bool in = u >= kPosMargin && u <= nxm - kPosMargin &&
+                                            v >= kPosMargin && v <= nym - kPosMargin;
+                            if (out) {
+                                decide = false;
+                            } else if (in) {
+                                const int32_t i0 = min((int32_t)floorf(u), T.nx - 2);
+                                const int32_t j0 = min((int32_t)floorf(v), T.ny - 2);
+                                const float fu = u - (float)i0, fv = v - (float)j0;
+                                const float* p = T.h + (int64_t)j0 * T.pitch + i0;
+                                const float h00 = __ldg(p), h10 = __ldg(p + 1);
+                                const float h01 = __ldg(p + T.pitch), h11 = __ldg(p + T.pitch + 1);
+                                const float top = h00 + fu * (h10 - h00);
+                                const float bot = h01 + fu * (h11 - h01);
+                                const float hb = top + fv * (bot - top);
+                                const float rng = fmaxf(fmaxf(h00, h10), fmaxf(h01, h11)) -
+                                                  fminf(fminf(h00, h10), fminf(h01, h11));
+                                decide = !((q.alt + rs) - hb > kLeafGuard + 0.01f * rng);
+                            }
+                        }
+                        if (decide) {
+                            bool ins;
+                            double uu, vv;
+                            if (below(T, C, d, (double)qj * a.step, ins, uu, vv)) {
+                                hit_k = qj;
+                                break;
+                            }
                         }
                     }
                     if (hit_k >= 0) break;
                 } else {
-                    const double ta = (double)ja * a.step, tb = (double)jb * a.step;
-                    const double xa[3] = { C[0] + ta * d[0], C[1] + ta * d[1], C[2] + ta * d[2] };
-                    const double xb[3] = { C[0] + tb * d[0], C[1] + tb * d[1], C[2] + tb * d[2] };
-                    double ua, va, ub, vb;
-                    if (!texel_image64(T, xa, ua, va) || !texel_image64(T, xb, ub, vb)) {
+                    const float ta = (float)ja * stepf, tb = (float)jb * stepf;
+                    float ua, va, ub, vb;
+                    if (!view_image_f(T, q, ta, rise_of<false>(q.rise, ta), ua, va) ||
+                        !view_image_f(T, q, tb, rise_of<false>(q.rise, tb), ub, vb)) {
                         descend = true;
                     } else {
-                        const double du = ub - ua, dv = vb - va;
-                        const double e = 1e-6 * (fabs(ua) + fabs(ub) + fabs(va) + fabs(vb) + 1.0) +
-                                         (du * du + dv * dv) * inv8r;
-                        const double lo_u = fmin(ua, ub) - e, hi_u = fmax(ua, ub) + e;
-                        const double lo_v = fmin(va, vb) - e, hi_v = fmax(va, vb) + e;
-                        const bool misses = hi_u < 0.0 || lo_u > (double)(T.nx - 1) ||
-                                            hi_v < 0.0 || lo_v > (double)(T.ny - 1);
+                        const float du = ub - ua, dv = vb - va;
+                        const float e = kPosMargin + (du * du + dv * dv) * inv8r;
+                        const float lo_u = fminf(ua, ub) - e, hi_u = fmaxf(ua, ub) + e;
+                        const float lo_v = fminf(va, vb) - e, hi_v = fmaxf(va, vb) + e;
+                        const bool misses = hi_u < 0.0f || lo_u > nxm || hi_v < 0.0f || lo_v > nym;
                         if (!misses) {
-                            const int32_t x0 = (int32_t)fmax(floor(lo_u), 0.0);
-                            const int32_t x1 = (int32_t)fmin(floor(hi_u) + 1.0, (double)(T.nx - 1));
-                            const int32_t y0 = (int32_t)fmax(floor(lo_v), 0.0);
-                            const int32_t y1 = (int32_t)fmin(floor(hi_v) + 1.0, (double)(T.ny - 1));
-                            const double M = (double)box_max(T, a.P, x0, x1, y0, y1);
-                            const double tc = fmin(fmax(tv, ta), tb);
-                            const double xc[3] = { C[0] + tc * d[0], C[1] + tc * d[1],
-                                                   C[2] + tc * d[2] };
-                            const double Hmin =
-                                sqrt(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]) - T.R;
-                            descend = !(Hmin - M > kViewGuard);
+                            const int32_t x0 = max(__float2int_rd(lo_u), 0);
+                            const int32_t x1 = min(__float2int_rd(hi_u) + 1, T.nx - 1);
+                            const int32_t y0 = max(__float2int_rd(lo_v), 0);
+                            const int32_t y1 = min(__float2int_rd(hi_v) + 1, T.ny - 1);
+                            const float M = box_max(T, a.P, x0, x1, y0, y1);
+                            const float tc = fminf(fmaxf(tv, ta), tb);
+                            const float Hmin = q.alt + rise_of<false>(q.rise, tc);
+                            descend = !(Hmin - M > kBlockGuard);
                         }
                     }
                 }
