@@ -155,7 +155,8 @@ typedef struct {
                               stepping 16)                                     */
     int32_t refill_min;    /* forward kernels: a warp's idle lanes take new
                               rays once at least this many are idle, in
-                              [0, 32]; 0 = default (exact descent 10, else 6)  */
+                              [0, 32]; 0 = default (exact descent: 14 with
+                              leaf tasks, 10 in single-lane walks; else 6)     */
     int32_t ray_tile_w;    /* grid-mode rays: w > 0 = a block's rays form
                               rectangles of w x (rays / w) texels (w must
                               divide the block's or chunk's ray count);

@@ -234,7 +234,6 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
                         : rays->mode == SS_RAYS_GRID   ? 24
                                                        : 32;
     a.rays_per_block = (int64_t)block * rpt;
-    a.refill_min = params->refill_min > 0 ? params->refill_min : (descent ? 10 : 6);
     a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
     a.tile_w = params->ray_tile_w;
     if (a.tile_w == 0 && descent && rays->mode == SS_RAYS_GRID &&
@@ -250,6 +249,14 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
               : params->strip_len > 0 ? params->strip_len
               : light_only ? 1 : kDefaultStrip;
     a.seed_w = params->seed_width > 0 ? params->seed_width : (rays->mode == SS_RAYS_GRID ? 1 : 2);
+    // warp services: the task descent (exact walks with column seeds on gnomonic
+    // tiles, see ss_forward.cuh) waits for 14 idle lanes, the single-lane walk
+    // for 10 (sweeps over sun directions and chunk shapes on the 4096^2 tile)
+    const bool tasks = descent && !light_only && hf->projection == SS_PROJ_GNOMONIC &&
+                       a.colseed && !(params->flags & SS_FLAG_LANE_LEAVES) &&
+                       a.kleaf <= (rays->mode == SS_RAYS_GRID ? 1 : 2) &&
+                       (rays->mode != SS_RAYS_GRID || a.tile_w > 0);
+    a.refill_min = params->refill_min > 0 ? params->refill_min : (tasks ? 14 : descent ? 10 : 6);
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);
