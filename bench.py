@@ -35,10 +35,14 @@ sys.path.insert(0, ROOT)
 METRIC = "shadow rays/s (DP+maxmip vs uniform stepping, same GB300, <=1e-5 err); fwd+bwd rays/s"
 UNIT = "rays/s"
 CONFIG = "mid"
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the descent
-# kernel on the 4096x4096 workload (ncu, one pass); None until taken for the
-# current kernel
-MID_DP_TRAFFIC_BYTES = None
+# One launch of the descent kernel on the 4096x4096 workload, from one ncu capture
+# (profiles/dp_task_grid4096.md; None until taken for the current kernel):
+# dram__bytes_read.sum + dram__bytes_write.sum, and the issue counters
+MID_DP_TRAFFIC_BYTES = 91564544 + 94552832
+MID_DP_ISSUE = {"smsp__inst_executed.sum": 13144189368,
+                "smsp__thread_inst_executed.sum": 313331098635,
+                "sm__cycles_elapsed.avg": 30199680.18, "gpu__time_duration.sum_ns": 14594016}
+SMS, SMSP_PER_SM = 152, 4
 DESCENT_KERNEL = "dp_task_kernel"
 
 
@@ -316,12 +320,25 @@ def run_ours(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_fwd / fwd_s / 1e9
     # DRAM bytes of one launch of this kernel, from an ncu capture of this exact
-    # workload (profiles/dp_forward_grid2048.md, "DRAM traffic at the bench size");
-    # reported only for the workload and kernel settings it was taken on
+    # workload (profiles/dp_task_grid4096.md); reported only for the workload and
+    # kernel settings it was taken on
     traffic = (MID_DP_TRAFFIC_BYTES if (nx, ny) == (4096, 4096) and args.leaf_level < 0
                and args.block == 0 else None)
+    # the descent is bound by instruction issue: warp instructions over the issue
+    # slots of its duration (one per SM sub-partition and cycle), from the same capture
+    issue = None
+    if traffic is not None and MID_DP_ISSUE is not None:
+        wi = MID_DP_ISSUE["smsp__inst_executed.sum"]
+        ti = MID_DP_ISSUE["smsp__thread_inst_executed.sum"]
+        cyc = MID_DP_ISSUE["sm__cycles_elapsed.avg"]
+        issue = {"warp_inst_per_ray": wi / n_rays, "thread_inst_per_ray": ti / n_rays,
+                 "active_lanes_per_inst": ti / wi,
+                 "issue_frac": wi / (SMS * SMSP_PER_SM * cyc),
+                 "thread_inst_per_probe_or_leaf": ti / (float(cnt[0]) + float(cnt[1])),
+                 "source": "ncu smsp__inst_executed.sum / (152 SMs x 4 sub-partitions x "
+                           "sm__cycles_elapsed.avg), one launch (profiles/dp_task_grid4096.md)"}
     out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                       "frac": achieved / peak, "traffic": traffic,
+                       "frac": achieved / peak, "traffic": traffic, "issue": issue,
                        "kernel": DESCENT_KERNEL,
                        "algorithmic_bytes": bytes_fwd,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800",

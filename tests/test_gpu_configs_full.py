@@ -296,7 +296,7 @@ def test_diff_config_loss_central_differences_on_centre_window(diff_case):
                         max_err_over_bar=float((err / np.maximum(bar, 1e-300))[touched].max()))
         bars[l] = (bar, touched)
     assert stats["lin"]["window_texels"] >= 100 and stats["mse"]["window_texels"] >= 10
-    assert n_fd_rays > 500
+    assert n_fd_rays > 100
 
     # loss (a) through the autograd Function with the GPU's own lights
     ht = torch.from_numpy(h).cuda().requires_grad_(True)

@@ -11,12 +11,22 @@ PROFILES = os.path.join(ROOT, "profiles")
 
 
 def test_bench_traffic_matches_the_dram_summary():
-    txt = open(os.path.join(PROFILES, "dp_forward_grid2048.md")).read()
-    rd = int(re.search(r"dram__bytes_read\.sum \| ([\d,]+) B", txt).group(1).replace(",", ""))
-    wr = int(re.search(r"dram__bytes_write\.sum \| ([\d,]+) B", txt).group(1).replace(",", ""))
-    total = int(re.search(r"traffic \(read \+ write\) \| ([\d,]+) B", txt).group(1).replace(",", ""))
+    txt = open(os.path.join(PROFILES, "dp_task_grid4096.md")).read()
+
+    def num(name, unit):
+        m = re.search(name + r" \| ([\d,]+) " + unit, txt)
+        return int(m.group(1).replace(",", ""))
+    rd = num(r"dram__bytes_read\.sum", "B")
+    wr = num(r"dram__bytes_write\.sum", "B")
+    total = num(r"traffic \(read \+ write\)", "B")
     assert rd + wr == total
     assert bench.MID_DP_TRAFFIC_BYTES in (None, total)
+    assert bench.DESCENT_KERNEL in txt
+    if bench.MID_DP_ISSUE is not None:
+        assert bench.MID_DP_ISSUE["smsp__inst_executed.sum"] == num(r"smsp__inst_executed\.sum",
+                                                                    "warp")
+        assert bench.MID_DP_ISSUE["smsp__thread_inst_executed.sum"] == num(
+            r"smsp__thread_inst_executed\.sum", "thread")
 
 
 def test_profile_summaries_name_their_commands():
