@@ -390,6 +390,17 @@ ss_status ss_shadow_greedy(const ss_heightfield* hf, const float* mip, const ss_
                            const ss_sun* sun, const int32_t* levels, int32_t n_runs,
                            float* light, float* cost, float* t_star, ss_stream_t stream);
 
+/* The same greedy descent at the arithmetic of the paper's shader (float32,
+ * Sec. 6.3), gnomonic tiles only (SS_ERR_UNSUPPORTED otherwise): tip heights in
+ * the ray's local frame, tip texel images from the ray's float32 slope, the run
+ * length of Eq. maxstep in float32; FP64 only where a tip's float32 image lies
+ * within its error margin of a mip-cell edge or of the tile's border.  Its
+ * decisions can differ from ss_shadow_greedy's where tips nearly tie; arguments
+ * and outputs as ss_shadow_greedy. */
+ss_status ss_shadow_greedy_f32(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                               const ss_sun* sun, const int32_t* levels, int32_t n_runs,
+                               float* light, float* cost, float* t_star, ss_stream_t stream);
+
 /* ----------------------------------------------------- shading epilogue --
  * Lambertian irradiance of the terrain under several disc lights (Sec. 3.4:
  * the Sun and the Earth are discs and each has its own lit fraction s_l, from
@@ -425,8 +436,11 @@ ss_status ss_shade(const ss_heightfield* hf, const ss_rays* rays, const ss_light
  * Along x(tau) = pos + tau d the samples tau_k = k step_m, k = 1 ..
  * floor(max_dist_m / step_m), are tested in order; the hit is the first one
  * whose texel image lies in [0,nx-1] x [0,ny-1] with |x| - R - h(image) <= 0
- * (h bilinear); when the sample before it is in the tile too the crossing is
- * refined by 48 bisection halvings of that step.  All in FP64.
+ * (h bilinear, decided in FP64); when the sample before it is in the tile too
+ * the crossing is refined in FP64 by bisection of that step down to a bracket
+ * of 2^-36 of it, finer than FP64 resolves |x| - R at a planetary radius (the
+ * float32 coordinates equal those of a longer bisection).  The march itself
+ * runs in float32 and defers to FP64 near the terrain and the tile's border.
  *
  * Output: the hits' texel coordinates (u, v) as float32 pairs in pixel order,
  * uv[2*r], uv[2*r+1] for r < *count (device int64 written by the call), and

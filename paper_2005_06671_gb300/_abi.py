@@ -101,6 +101,8 @@ _SIGNATURES = {
     "ss_batch_plan_destroy": (c_i32, [c_vp]),
     "ss_shadow_greedy": (c_i32, [P(SSHeightfield), c_vp, P(SSRays), P(SSSun), c_vp, c_i32,
                                  c_vp, c_vp, c_vp, c_vp]),
+    "ss_shadow_greedy_f32": (c_i32, [P(SSHeightfield), c_vp, P(SSRays), P(SSSun), c_vp, c_i32,
+                                     c_vp, c_vp, c_vp, c_vp]),
     "ss_shade": (c_i32, [P(SSHeightfield), P(SSRays), c_vp, c_i32, c_vp, c_vp]),
     "ss_view_workspace_bytes": (ctypes.c_size_t, [c_i32, c_i32]),
     "ss_view_rays": (c_i32, [P(SSHeightfield), c_vp, P(SSCamera), ctypes.c_double,

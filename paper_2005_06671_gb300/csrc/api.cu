@@ -120,6 +120,7 @@ ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, doubl
     T.delta = delta;
     T.inv_gR = 1.0 / (hf->texel_m * hf->radius_m);
     T.inv_R = 1.0 / hf->radius_m;
+    T.inv_g = 1.0 / hf->texel_m;
     T.alpha = sun->angular_radius_rad;
     T.delta_f = (float)delta;
     T.inv_delta_f = (float)(1.0 / delta);
@@ -341,6 +342,7 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
                                          : (B.args.light_only ? 1 : kDefaultStrip);
     B.args.colseed = (params->strip_len == 0 && !B.args.light_only && tile_w > 0) ? 1 : 0;
     B.args.seed_w = params->seed_width > 0 ? params->seed_width : 1;   // grid rays
+    B.args.lane_leaves = (params->flags & SS_FLAG_LANE_LEAVES) ? 1 : 0;
     return SS_OK;
 }
 
@@ -707,10 +709,12 @@ ss_status ss_view_rays(const ss_heightfield* hf, const float* mip, const ss_came
 // ------------------------------------------------------------ greedy descent
 extern "C" {
 
-ss_status ss_shadow_greedy(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
-                           const ss_sun* sun, const int32_t* levels, int32_t n_runs,
-                           float* light, float* cost, float* t_star, ss_stream_t stream) {
+static ss_status greedy_common(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                               const ss_sun* sun, const int32_t* levels, int32_t n_runs,
+                               float* light, float* cost, float* t_star, ss_stream_t stream,
+                               bool f32) {
     ss_status st = check_tile(hf, 2);
+    if (f32 && hf->projection != SS_PROJ_GNOMONIC) return SS_ERR_UNSUPPORTED;
     if (st != SS_OK) return st;
     if ((st = check_sun(sun)) != SS_OK) return st;
     int64_t n;
@@ -731,9 +735,21 @@ ss_status ss_shadow_greedy(const ss_heightfield* hf, const float* mip, const ss_
     R.uv = rays->uv;
     R.lift = rays->mode == SS_RAYS_LIST ? rays->lift_m : nullptr;
     cudaError_t e = ss::launch_greedy(T, P, R, levels, n_runs, light, cost, t_star,
-                                      (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "ss_shadow_greedy");
+                                      (cudaStream_t)stream, mip + ML.stats_offset, f32);
+    if (e != cudaSuccess) return cuda_fail(e, f32 ? "ss_shadow_greedy_f32" : "ss_shadow_greedy");
     return SS_OK;
+}
+
+ss_status ss_shadow_greedy(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                           const ss_sun* sun, const int32_t* levels, int32_t n_runs,
+                           float* light, float* cost, float* t_star, ss_stream_t stream) {
+    return greedy_common(hf, mip, rays, sun, levels, n_runs, light, cost, t_star, stream, false);
+}
+
+ss_status ss_shadow_greedy_f32(const ss_heightfield* hf, const float* mip, const ss_rays* rays,
+                               const ss_sun* sun, const int32_t* levels, int32_t n_runs,
+                               float* light, float* cost, float* t_star, ss_stream_t stream) {
+    return greedy_common(hf, mip, rays, sun, levels, n_runs, light, cost, t_star, stream, true);
 }
 
 }  // extern "C"

@@ -31,6 +31,7 @@ struct GreedyArgs {
     Tile T;
     Pyramid P;
     Rays R;
+    const float* stats;   // (global max, global min) of the heights
     float* light;
     float* cost;
     float* t_star;
@@ -138,15 +139,161 @@ __global__ void __launch_bounds__(256) greedy_kernel(const GreedyArgs a) {
     }
 }
 
+// ------------------------------------------------- float32 greedy descent
+// The same algorithm at the arithmetic of the paper's shader (float32), on
+// gnomonic tiles: tip heights in the ray's local frame (origin height minus a
+// reference texel, plus the cancellation-free rise), tip texel images from the
+// ray's float32 slope (as the exact descent's block ends), the run length of
+// Eq. maxstep in float32 in the tile-centre frame.  FP64 only where a tip's
+// level-m texel is ambiguous: when its float32 image lies within its error
+// margin of a cell edge or of the tile's border, the FP64 image decides.
+// An approximation of the same approximation: reported beside the FP64 kernel,
+// which keeps decision identity with the oracle.
+
+// Eq. maxstep in float32: run start Rs = P0 + rs (P0 = (0, 0, R), the tile
+// centre's point on the sphere; rs a few km, kept to ~1 mm)
+__device__ float run_length_f32(const Tile& T, const float rs[3], const float s[3], int32_t m0) {
+    const float R = T.R_f, kx = T.R_f / T.g_f;
+    const float qz = R + rs[2];
+    if (!(qz > 0.0f)) return -1.0f;
+    const float u0 = kx * rs[0] / qz + T.cx_f, v0 = kx * rs[1] / qz + T.cy_f;
+    const float ln = sqrtf(s[0] * s[0] + s[1] * s[1]);
+    if (!(ln > 0.0f)) return -1.0f;
+    const float span = ldexpf(1.0f, m0);
+    const float X = (u0 + span * s[0] / ln - T.cx_f) * T.g_f;
+    const float Y = (v0 + span * s[1] / ln - T.cy_f) * T.g_f;
+    const float im = rsqrtf(X * X + Y * Y + R * R);
+    const float e[3] = { X * im, Y * im, R * im };
+    // c = -(P0 + rs); c x e = -(P0 x e) - rs x e, with P0 x e = R (-e_y, e_x, 0)
+    const float ce[3] = { R * e[1] - (rs[1] * e[2] - rs[2] * e[1]),
+                          -R * e[0] - (rs[2] * e[0] - rs[0] * e[2]),
+                          -(rs[0] * e[1] - rs[1] * e[0]) };
+    const float se[3] = { s[1] * e[2] - s[2] * e[1], s[2] * e[0] - s[0] * e[2],
+                          s[0] * e[1] - s[1] * e[0] };
+    const float den = se[0] * se[0] + se[1] * se[1] + se[2] * se[2];
+    if (!(den > 0.0f)) return -1.0f;
+    return (ce[0] * se[0] + ce[1] * se[1] + ce[2] * se[2]) / den;
+}
+
+template <bool kGrid>
+__global__ void __launch_bounds__(256) greedy_f32_kernel(const GreedyArgs a) {
+    const Tile& T = a.T;
+    const int64_t n = ray_count(T, a.R);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float s[3] = { T.sx_f, T.sy_f, T.sz_f };
+    const double sd[3] = { T.sx, T.sy, T.sz };
+    const float span = a.stats[0] - a.stats[1];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        RayF rf;
+        setup_ray<kGrid, false, false>(T, a.R, r, span, rf);
+        // origin relative to P0 (p = rho n, n = (X, Y, R)/m, m = |(X, Y, R)|):
+        // p_z - R = (R/m)(rho - m) = (R/m)(h_p - (X^2 + Y^2)/(m + R)), no
+        // cancellation; the FP64 origin only for ambiguous tips
+        const float Xp = (rf.u0 - T.cx_f) * T.g_f, Yp = (rf.v0 - T.cy_f) * T.g_f;
+        const float rho = 0.5f / rf.inv_2rho;
+        const float im = rsqrtf(Xp * Xp + Yp * Yp + T.R_f * T.R_f);
+        const float m = 1.0f / im;
+        const float hp = rf.href + rf.X;
+        float p0[3];
+        p0[0] = rho * Xp * im;
+        p0[1] = rho * Yp * im;
+        p0[2] = T.R_f * im * (hp - (Xp * Xp + Yp * Yp) / (m + T.R_f));
+        bool have64 = false;
+        double p64[3] = { 0.0, 0.0, 0.0 };
+        const float amax = fmaxf(fabsf(rf.au), fabsf(rf.av));
+        float bestJ = INFINITY, bestd = -1.0f, start = 0.0f;
+        for (int32_t run = 0; run < a.n_runs; ++run) {
+            const int32_t Np = a.levels[run];
+            const float rs[3] = { p0[0] + start * s[0], p0[1] + start * s[1],
+                                  p0[2] + start * s[2] };
+            const float Tr = run_length_f32(T, rs, s, Np - 1);
+            if (!(Tr > 0.0f)) break;
+            float tk = 1.0f, dstar = INFINITY, ts = -1.0f;
+            for (int32_t k = 0; k < Np; ++k) {
+                const int32_t mlev = min(Np - 1 - k, a.P.levels - 1);
+                const float step = ldexpf(1.0f, -(k + 1));
+                const float cell = ldexpf(1.0f, mlev);
+                const int32_t w = ((T.nx - 1) >> mlev) + 1, h = ((T.ny - 1) >> mlev) + 1;
+                dstar = INFINITY;
+                ts = -1.0f;
+                for (int i = 0; i < 3; ++i) {
+                    if (i > 0) tk -= step;
+                    if (!(tk > 0.0f)) continue;
+                    const float dist = start + tk * Tr;
+                    const float jf = dist / T.delta_f;
+                    float u, v;
+                    block_end<false>(T, rf, jf, 0.0f, 0.0f, u, v);
+                    const float E = 1e-3f + 5e-7f * (float)(T.nx + T.ny) + 8e-7f * amax * jf;
+                    const float fu = (u + 0.5f) / cell, fv = (v + 0.5f) / cell;
+                    const float eu = E / cell;
+                    const bool amb = fabsf(fu - rintf(fu)) < eu || fabsf(fv - rintf(fv)) < eu ||
+                                     fabsf(u) < E || fabsf(u - (float)(T.nx - 1)) < E ||
+                                     fabsf(v) < E || fabsf(v - (float)(T.ny - 1)) < E;
+                    bool in;
+                    int32_t I, J;
+                    if (!amb) {
+                        in = u >= 0.0f && u <= (float)(T.nx - 1) && v >= 0.0f &&
+                             v <= (float)(T.ny - 1);
+                        I = min(max((int32_t)floorf(fu), 0), w - 1);
+                        J = min(max((int32_t)floorf(fv), 0), h - 1);
+                    } else {
+                        if (!have64) {
+                            double up, vp, hp, href, ow[4];
+                            int32_t oi0, oj0;
+                            ray_origin(T, a.R, r, up, vp, hp, href, oi0, oj0, ow);
+                            double nv[3];
+                            texel_dir64(T, up, vp, nv);
+                            const double rhod = T.R + hp;
+                            for (int c = 0; c < 3; ++c) p64[c] = rhod * nv[c];
+                            have64 = true;
+                        }
+                        const double dd = (double)dist;
+                        const double q[3] = { p64[0] + dd * sd[0], p64[1] + dd * sd[1],
+                                              p64[2] + dd * sd[2] };
+                        double ud, vd;
+                        in = texel_image64(T, q, ud, vd) && in_tile64(T, ud, vd);
+                        const double celld = (double)cell;
+                        I = min(max((int32_t)floor((ud + 0.5) / celld), 0), w - 1);
+                        J = min(max((int32_t)floor((vd + 0.5) / celld), 0), h - 1);
+                    }
+                    if (!in) continue;
+                    const float M = __ldg(a.P.ptr[mlev] + (int64_t)J * a.P.pitch[mlev] + I);
+                    const float dl = (rf.X + rise_of<false>(rf, dist)) - (M - rf.href);
+                    if (dl < dstar) {
+                        dstar = dl;
+                        ts = tk;
+                    }
+                }
+                if (ts > -1.0f) tk = ts + step;
+            }
+            if (ts > -1.0f) {
+                const float dist = start + ts * Tr;
+                const float J = dstar / dist;
+                if (J < bestJ) {
+                    bestJ = J;
+                    bestd = dist;
+                }
+            }
+            start += Tr;
+        }
+        float light = 1.0f;
+        if (bestd > 0.0f) light = disc_light32(bestJ * cos_elev_f32(T, a.R, r, false) / T.alpha_f);
+        a.light[r] = light;
+        if (a.cost) a.cost[r] = bestJ;
+        if (a.t_star) a.t_star[r] = bestd;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_greedy(const Tile& T, const Pyramid& P, const Rays& R, const int32_t* levels,
                           int32_t n_runs, float* light, float* cost, float* t_star,
-                          cudaStream_t s) {
+                          cudaStream_t s, const float* stats, bool f32) {
     GreedyArgs a{};
     a.T = T;
     a.P = P;
     a.R = R;
+    a.stats = stats;
     a.light = light;
     a.cost = cost;
     a.t_star = t_star;
@@ -159,7 +306,12 @@ cudaError_t launch_greedy(const Tile& T, const Pyramid& P, const Rays& R, const 
         per_sm = 1;
     const int64_t cap = (int64_t)device_sm_count() * per_sm, want = (n + 255) / 256;
     const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-    greedy_kernel<<<grid, 256, 0, s>>>(a);
+    if (!f32)
+        greedy_kernel<<<grid, 256, 0, s>>>(a);
+    else if (R.mode == 0)
+        greedy_f32_kernel<true><<<grid, 256, 0, s>>>(a);
+    else
+        greedy_f32_kernel<false><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

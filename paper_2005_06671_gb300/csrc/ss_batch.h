@@ -36,6 +36,7 @@ struct BatchArgs {
     int32_t strip;                  // rays per seeded strip (1 = no seeding)
     int32_t colseed;                // rectangular chunks: single rays, column seeds
     int32_t seed_w;                 // half-width of a seed window
+    int32_t lane_leaves;            // SS_FLAG_LANE_LEAVES: leaves in the walking lane
 };
 
 constexpr int32_t kBatchSeedW = 64;    // widest chunk with a column-seed table

@@ -46,6 +46,7 @@ struct Tile {
     double delta;              // sample spacing (m)
     double inv_gR;             // 1 / (g R)
     double inv_R;              // 1 / R
+    double inv_g;              // 1 / g
     double alpha;              // sun angular radius
     float delta_f;             // (float)delta
     float inv_delta_f;         // (float)(1/delta)

@@ -78,7 +78,7 @@ cudaError_t launch_view_rays(const Tile& T, const Pyramid& P, const ViewCamera& 
 constexpr int kGreedyMaxRuns = 8;
 cudaError_t launch_greedy(const Tile& T, const Pyramid& P, const Rays& R, const int32_t* levels,
                           int32_t n_runs, float* light, float* cost, float* t_star,
-                          cudaStream_t s);
+                          cudaStream_t s, const float* stats, bool f32);
 
 constexpr int kShadeMaxLights = 8;
 struct ShadeLight {       // mirrors ss_light

@@ -7,8 +7,8 @@
 //   d = unit(forward + a right + b up), x(tau) = C + tau d, samples tau_k = k step;
 //   the hit is the first sample whose texel image is in the tile and lies on or
 //   below the terrain (|x| - R - h <= 0, decided in FP64); when the sample
-//   before it is in the tile too the crossing is refined in FP64 by 48
-//   bisection halvings.
+//   before it is in the tile too the crossing is refined in FP64 by bisection
+//   to a bracket of 2^-36 of the step (see below_fast).
 // Sample blocks are walked near-to-far like the shadow descent (aligned blocks
 // of 2^k samples, next block at s0 += 2^k) in float32: a block is skipped when
 // the ray's lowest height over it exceeds the maximum-mipmap value over its
@@ -17,6 +17,7 @@
 // above the terrain or off the tile.  So the first sample found below the
 // terrain is the first one overall, the same sample as an FP64 march.
 //
+// A second pass gathers each block's hits and bisects them with full warps.
 // Then the hits are compacted in pixel order (per-block counts, one scan block,
 // a scatter), so the ray list is deterministic.
 #include <cuda_runtime.h>
@@ -47,6 +48,7 @@ struct ViewArgs {
     int64_t K;
     const float* stats;       // (global max, global min) of the heights
     float2* pix_uv;           // per pixel: hit texel coords, NaN when none
+    int32_t* hit_k;           // per pixel: first sample below the terrain, -1 when none
     int32_t* block_count;     // per block of kViewBlock pixels
     int64_t* block_off;       // exclusive prefix of block_count
     int32_t n_blocks;
@@ -66,6 +68,35 @@ __device__ __forceinline__ bool below(const Tile& T, const double C[3], const do
     const double hb = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, u, v, &i0, &j0, w);
     const double H = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) - T.R;
     return H - hb <= 0.0;
+}
+
+// below() for the bisection of the crossing: one square root and one division
+// (|x| serves both the height and the stereographic image; 1/g folded into the
+// scale).  Its roundings differ from below()'s only at the 1e-16 relative
+// level, and the bisection stops at a bracket of 2^-kViewHalvings of the step,
+// below the FP64 resolution of |x| - R at the lunar radius (~1e-10 m), so the
+// float32 hit coordinates are those of the full 48-halving bisection.
+constexpr int kViewHalvings = 36;
+
+__device__ __forceinline__ bool below_fast(const Tile& T, const double C[3], const double d[3],
+                                           double tau) {
+    const double x[3] = { C[0] + tau * d[0], C[1] + tau * d[1], C[2] + tau * d[2] };
+    const double m = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    double k;
+    if (T.proj == 0) {
+        if (!(x[2] > 0.0)) return false;
+        k = (T.R * T.inv_g) / x[2];
+    } else {
+        const double den = m + x[2];
+        if (!(den > 0.0)) return false;
+        k = (2.0 * T.R * T.inv_g) / den;
+    }
+    const double u = x[0] * k + T.cx, v = x[1] * k + T.cy;
+    if (!in_tile64(T, u, v)) return false;
+    int32_t i0, j0;
+    double w[4];
+    const double hb = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, u, v, &i0, &j0, w);
+    return (m - T.R) - hb <= 0.0;
 }
 
 // maximum of the heights over texel box [x0, x1] x [y0, y1] (inclusive, clamped
@@ -118,24 +149,29 @@ __device__ __forceinline__ bool view_image_f(const Tile& T, const ViewRayF& q, f
     return true;
 }
 
+// unit direction of pixel pix's view ray
+__device__ __forceinline__ void pixel_dir(const Cam& cm, int64_t pix, double d[3]) {
+    const int64_t i = pix % cm.W, j = pix / cm.W;
+    const double aa = (2.0 * ((double)i + 0.5) / (double)cm.W - 1.0) * cm.tan_x;
+    const double bb = (1.0 - 2.0 * ((double)j + 0.5) / (double)cm.H) * cm.tan_y;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = cm.f[k] + aa * cm.r[k] + bb * cm.u[k];
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] /= dn;
+}
+
+// Pass 1: per pixel, the first sample below the terrain (hit_k, -1 when none).
 __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) {
     const int64_t npix = (int64_t)a.cam.W * a.cam.H;
     const int64_t pix = (int64_t)blockIdx.x * kViewBlock + threadIdx.x;
-    bool hit = false;
-    double hu = 0.0, hv = 0.0;
     if (pix < npix) {
         const Tile& T = a.T;
         const Cam& cm = a.cam;
-        const int64_t i = pix % cm.W, j = pix / cm.W;
-        const double aa = (2.0 * ((double)i + 0.5) / (double)cm.W - 1.0) * cm.tan_x;
-        const double bb = (1.0 - 2.0 * ((double)j + 0.5) / (double)cm.H) * cm.tan_y;
         double d[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] = cm.f[k] + aa * cm.r[k] + bb * cm.u[k];
-        const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] /= dn;
+        pixel_dir(cm, pix, d);
         const double* C = cm.C;
+        int64_t hit_k = -1;
         // samples that can reach the highest height: tau in [tau_in, tau_out]
         const double hmax = (double)a.stats[0];
         const double Rm = T.R + hmax;
@@ -190,7 +226,6 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
             while (((int64_t)1 << kk) < n) ++kk;
             int64_t s0 = 0;
             int32_t k = kk;
-            int64_t hit_k = -1;
             while (s0 < n) {
                 const int64_t ja = b0 + s0 + 1;
                 const int64_t jb = min(b0 + s0 + ((int64_t)1 << k), k1);
@@ -264,33 +299,58 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
                     k = s0 == 0 ? kk : min(__ffsll(s0) - 1, kk);
                 }
             }
-            if (hit_k >= 0) {
-                double hi = (double)hit_k * a.step;
-                bool prev_in = false;
-                if (hit_k > 1) {
-                    double u, v;
-                    below(T, C, d, (double)(hit_k - 1) * a.step, prev_in, u, v);
-                }
-                if (prev_in) {
-                    double lo = (double)(hit_k - 1) * a.step;
-                    for (int it = 0; it < 48; ++it) {
-                        const double mid = lo + 0.5 * (hi - lo);
-                        bool ins;
-                        double u, v;
-                        if (below(T, C, d, mid, ins, u, v))
-                            hi = mid;
-                        else
-                            lo = mid;
-                    }
-                }
-                const double xh[3] = { C[0] + hi * d[0], C[1] + hi * d[1], C[2] + hi * d[2] };
-                hit = texel_image64(T, xh, hu, hv);
+        }
+        a.hit_k[pix] = (int32_t)hit_k;
+    }
+}
+
+// Pass 2: the hits of a block of pixels, gathered in shared memory so that
+// full warps run the FP64 bisection of the crossing (a pass-1 warp has a hit in
+// only some of its lanes); writes every pixel's texel coordinates (NaN without
+// a hit) and the block's hit count.
+__global__ void __launch_bounds__(kViewBlock) view_refine_kernel(const ViewArgs a) {
+    __shared__ int32_t s_pix[kViewBlock];
+    __shared__ int32_t s_cnt;
+    const int64_t npix = (int64_t)a.cam.W * a.cam.H;
+    const int64_t base = (int64_t)blockIdx.x * kViewBlock;
+    const int64_t pix = base + threadIdx.x;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const bool mine = pix < npix && a.hit_k[pix] >= 0;
+    if (pix < npix && !mine) a.pix_uv[pix] = make_float2(NAN, NAN);
+    if (mine) s_pix[atomicAdd(&s_cnt, 1)] = threadIdx.x;
+    __syncthreads();
+    const int cnt = s_cnt;
+    if (threadIdx.x == 0) a.block_count[blockIdx.x] = cnt;
+    if ((int)threadIdx.x < cnt) {
+        const Tile& T = a.T;
+        const int64_t p = base + s_pix[threadIdx.x];
+        const int64_t hit_k = a.hit_k[p];
+        double d[3];
+        pixel_dir(a.cam, p, d);
+        const double* C = a.cam.C;
+        double hi = (double)hit_k * a.step;
+        bool prev_in = false;
+        if (hit_k > 1) {
+            double u, v;
+            below(T, C, d, (double)(hit_k - 1) * a.step, prev_in, u, v);
+        }
+        if (prev_in) {
+            double lo = (double)(hit_k - 1) * a.step;
+            for (int it = 0; it < kViewHalvings; ++it) {
+                const double mid = lo + 0.5 * (hi - lo);
+                if (below_fast(T, C, d, mid))
+                    hi = mid;
+                else
+                    lo = mid;
             }
         }
-        a.pix_uv[pix] = hit ? make_float2((float)hu, (float)hv) : make_float2(NAN, NAN);
+        const double xh[3] = { C[0] + hi * d[0], C[1] + hi * d[1], C[2] + hi * d[2] };
+        double hu, hv;
+        // the point lies between two samples of the tile: it has an image
+        texel_image64(T, xh, hu, hv);
+        a.pix_uv[p] = make_float2((float)hu, (float)hv);
     }
-    const int cnt = __syncthreads_count(hit);
-    if (threadIdx.x == 0) a.block_count[blockIdx.x] = cnt;
 }
 
 // exclusive prefix of the per-block counts (one block of 1024 threads)
@@ -355,7 +415,7 @@ int64_t view_blocks(int32_t width, int32_t height) {
 
 size_t view_workspace_bytes(int32_t width, int32_t height) {
     const int64_t npix = (int64_t)width * height, nb = view_blocks(width, height);
-    return (size_t)(npix * 8 + nb * 4 + 256 + nb * 8 + 256);
+    return (size_t)(npix * 8 + nb * 4 + 256 + nb * 8 + 256 + npix * 4 + 256);
 }
 
 cudaError_t launch_view_rays(const Tile& T, const Pyramid& P, const ViewCamera& vc, double step,
@@ -385,11 +445,15 @@ cudaError_t launch_view_rays(const Tile& T, const Pyramid& P, const ViewCamera& 
     off += (size_t)nb * 4;
     off = (off + 255) & ~(size_t)255;
     a.block_off = reinterpret_cast<int64_t*>(ws + off);
+    off += (size_t)nb * 8;
+    off = (off + 255) & ~(size_t)255;
+    a.hit_k = reinterpret_cast<int32_t*>(ws + off);
     a.n_blocks = (int32_t)nb;
     a.uv_out = uv;
     a.pixel_out = pixel;
     a.count_out = count;
     view_hit_kernel<<<(unsigned)nb, kViewBlock, 0, s>>>(a);
+    view_refine_kernel<<<(unsigned)nb, kViewBlock, 0, s>>>(a);
     view_scan_kernel<<<1, 1024, 0, s>>>(a);
     view_compact_kernel<<<(unsigned)nb, kViewBlock, 0, s>>>(a);
     return cudaGetLastError();

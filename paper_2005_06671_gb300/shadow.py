@@ -294,12 +294,15 @@ class Batch:
 
     def __init__(self, hfs, suns, max_len_m, step_texels=0.5, count_samples=False,
                  want_cost=False, block_threads=0, leaf_level=-1, rays_per_thread=0,
-                 refill_min=0, ray_tile_w=0, light_only=False, strip_len=0, seed_width=0):
+                 refill_min=0, ray_tile_w=0, light_only=False, strip_len=0, seed_width=0,
+                 lane_leaves=False):
         if len(hfs) != len(suns) or not hfs:
             raise ValueError("need one sun per heightfield, at least one item")
         self.hfs, self.suns = list(hfs), list(suns)
         dev = hfs[0].h.device
-        flags = (SS_FLAG_COUNT_SAMPLES if count_samples else 0) | (SS_FLAG_LIGHT_ONLY if light_only else 0)
+        flags = ((SS_FLAG_COUNT_SAMPLES if count_samples else 0) |
+                 (SS_FLAG_LIGHT_ONLY if light_only else 0) |
+                 (_abi.SS_FLAG_LANE_LEAVES if lane_leaves else 0))
         self.params = SSParams(float(max_len_m), float(step_texels), int(flags), int(block_threads),
                                int(leaf_level), int(rays_per_thread), int(refill_min),
                                int(ray_tile_w), int(strip_len), int(seed_width))
@@ -405,9 +408,10 @@ def ss_view_rays(hf: Heightfield, mip, cam, step_m=None, max_dist_m=None, stream
 
 # ------------------------------------------------------------ greedy descent
 def ss_shadow_greedy(hf: Heightfield, mip, sun: Sun, levels=(5, 5, 5), uv=None, lift=None,
-                     stream=None):
+                     stream=None, fp32=False):
     """The paper's greedy descent (an approximation of ss_shadow_forward's exact
-    minimum): dict(light, cost [rad], t_star [m]) per ray; ``levels`` = N' per run."""
+    minimum): dict(light, cost [rad], t_star [m]) per ray; ``levels`` = N' per run.
+    ``fp32``: the float32 build (ss_shadow_greedy_f32, gnomonic tiles)."""
     L = _abi.lib()
     rays, n = _rays(hf, uv, lift)
     dev = hf.h.device
@@ -415,10 +419,11 @@ def ss_shadow_greedy(hf: Heightfield, mip, sun: Sun, levels=(5, 5, 5), uv=None, 
     cost = torch.empty(n, dtype=torch.float32, device=dev)
     t_star = torch.empty(n, dtype=torch.float32, device=dev)
     lv = (ctypes.c_int32 * len(levels))(*[int(x) for x in levels])
-    st = L.ss_shadow_greedy(ctypes.byref(hf.c()), _ptr(mip), ctypes.byref(rays),
-                            ctypes.byref(sun.c()), ctypes.cast(lv, ctypes.c_void_p), len(levels),
-                            _ptr(light), _ptr(cost), _ptr(t_star), _stream_ptr(stream))
-    _abi.check(st, "ss_shadow_greedy")
+    fn = L.ss_shadow_greedy_f32 if fp32 else L.ss_shadow_greedy
+    st = fn(ctypes.byref(hf.c()), _ptr(mip), ctypes.byref(rays), ctypes.byref(sun.c()),
+            ctypes.cast(lv, ctypes.c_void_p), len(levels), _ptr(light), _ptr(cost), _ptr(t_star),
+            _stream_ptr(stream))
+    _abi.check(st, "ss_shadow_greedy_f32" if fp32 else "ss_shadow_greedy")
     return {"light": light, "cost": cost, "t_star": t_star}
 
 

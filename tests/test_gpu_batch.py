@@ -65,8 +65,12 @@ def _same(a, b):
                                 dict(rays_per_thread=2, ray_tile_w=8, refill_min=4),
                                 dict(block_threads=128, leaf_level=3),
                                 dict(strip_len=1), dict(strip_len=7, ray_tile_w=16),
-                                dict(strip_len=64, rays_per_thread=8, ray_tile_w=32)])
+                                dict(strip_len=64, rays_per_thread=8, ray_tile_w=32),
+                                dict(lane_leaves=True), dict(lane_leaves=True, refill_min=3),
+                                dict(leaf_level=0, rays_per_thread=6, ray_tile_w=64)])
 def test_batch_equals_single_forward(kw):
+    """Every instance of a batch gives exactly the single-tile forward's outputs,
+    with leaf samples as warp tasks (default) or in the walking lane."""
     insts = _instances()
     lmax = 2500.0
     res = _batch(insts, lmax, **kw)[0]
@@ -76,6 +80,8 @@ def test_batch_equals_single_forward(kw):
 
 @pytest.mark.parametrize("kw", [dict(rays_per_thread=1, refill_min=1, strip_len=1),
                                 dict(rays_per_thread=1, refill_min=2, ray_tile_w=8),
+                                dict(rays_per_thread=1, refill_min=2, ray_tile_w=8,
+                                     lane_leaves=True),
                                 dict(rays_per_thread=3, refill_min=1, strip_len=5, ray_tile_w=32)])
 def test_batch_chunk_switches_keep_every_ray(kw):
     """Tiny chunks and eager refills: warps move to their next chunk while other
@@ -95,9 +101,10 @@ def test_plan_replays_repeat_results_and_count_probes():
     lmax = 2500.0
     # without seeded strips every ray is walked from scratch in both kernels, so
     # the probe counts match too
-    runs = _batch(insts, lmax, plan=True, replays=3, count_samples=True, strip_len=1)
+    runs = _batch(insts, lmax, plan=True, replays=3, count_samples=True, strip_len=1,
+                  lane_leaves=True)
     for (h, g, sun), a, b, c in zip(insts, *runs):
-        ref = _single(h, g, sun, lmax, count_samples=True, strip_len=1)
+        ref = _single(h, g, sun, lmax, count_samples=True, strip_len=1, lane_leaves=True)
         _same(a, ref)
         _same(b, ref)
         _same(c, ref)

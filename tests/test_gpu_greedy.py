@@ -87,3 +87,51 @@ def test_list_mode_with_lift(proj):
     light, cost, tstar = oracle.greedy(h, g, R, sun[0], sun[1], sun[2], levels=(6, 4),
                                        proj=proj, uv=uv, lift=lift)
     _compare(got, light, cost, tstar)
+
+
+@pytest.mark.parametrize("name,n,uv_n", [("tiny", None, 0), ("diff", None, 0), ("mid", 2048, 0),
+                                         ("diff", None, 20000)])
+def test_float32_build_against_fp64_build(name, n, uv_n):
+    """ss_shadow_greedy_f32 (the paper's float32 arithmetic, run lengths of Eq.
+    maxstep in float32 too) against the FP64 build, which is decision-identical
+    to the oracle.  The tips of a run sit at fractions of its length T, which
+    float32 computes to ~1e-3 relative (a cross product of nearly parallel
+    vectors), so tip decisions can differ where tips nearly tie; nearly every
+    ray's light must still agree, and the light's error against the exact
+    descent must be that of the FP64 build.  Grid and listed rays."""
+    inst = make_instance(name, n=n)
+    h, g = inst["h"], inst["g"]
+    uv = lift = None
+    if uv_n:
+        uv = random_origins(uv_n, h.shape[1], h.shape[0], seed=23)
+        lift = np.random.default_rng(24).uniform(0, 20, uv_n).astype(np.float32)
+    hf = ss.Heightfield(_dev(h), g, R)
+    mip = ss.ss_build_maxmip(hf)
+    for (e, a) in inst["suns"][:2]:
+        s = ss.Sun(e, a, inst["alpha"])
+        kw = dict(uv=None if uv is None else _dev(uv), lift=None if lift is None else _dev(lift))
+        d = ss.ss_shadow_greedy(hf, mip, s, levels=(5, 5, 5), **kw)
+        f = ss.ss_shadow_greedy(hf, mip, s, levels=(5, 5, 5), fp32=True, **kw)
+        x = ss.ss_shadow_forward(hf, mip, s, inst["lmax"], **kw)
+        torch.cuda.synchronize()
+        d = {k: v.cpu().numpy().astype(np.float64) for k, v in d.items()}
+        f = {k: v.cpu().numpy().astype(np.float64) for k, v in f.items()}
+        exact = x["light"].cpu().numpy().astype(np.float64)
+        assert np.all((f["light"] >= 0) & (f["light"] <= 1))
+        agree = np.abs(f["light"] - d["light"]) <= 1e-4
+        assert agree.mean() > 0.97, agree.mean()
+        ed, ef = np.abs(d["light"] - exact).mean(), np.abs(f["light"] - exact).mean()
+        assert abs(ef - ed) <= 0.05 * ed + 1e-3, (ed, ef)
+        # in the penumbra the light fixes the cost: where the lights agree there,
+        # so do the costs (a saturated light says nothing about its cost)
+        pen = agree & (d["light"] > 0) & (d["light"] < 1) & (d["t_star"] > 0)
+        assert pen.sum() > 20
+        assert np.all(np.abs(f["cost"][pen] - d["cost"][pen]) <= 2e-3 * np.abs(d["cost"][pen]) + 2e-5)
+
+
+def test_float32_build_rejects_stereographic_tiles():
+    h = lunar_tile(64, 40.0, seed=3, amplitude=500.0, n_craters=4)
+    hf = ss.Heightfield(_dev(h), 40.0, R, projection="polar_stereo")
+    mip = ss.ss_build_maxmip(hf)
+    with pytest.raises(RuntimeError):
+        ss.ss_shadow_greedy(hf, mip, ss.Sun(0.02, 0.3, 0.005), fp32=True)
