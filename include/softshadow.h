@@ -106,10 +106,11 @@ enum { SS_RAYS_GRID = 0, SS_RAYS_LIST = 1 };
 
 /* ss_shadow_backward_ws: deterministic accumulation (see there). */
 #define SS_FLAG_DETERMINISTIC_BWD 0x8u
-/* ss_shadow_forward, grid rays on gnomonic tiles: by default a warp evaluates
- * the leaf samples its lanes' walks cannot prune as shared tasks, 32 at a time
- * (the walks themselves only bound blocks); with this flag each lane evaluates
- * its own ray's leaf samples inside its walk.  Same results bit for bit. */
+/* ss_shadow_forward, exact descent with column seeds (the default): a warp
+ * evaluates the leaf samples its lanes' walks cannot prune as shared tasks, 32
+ * at a time (the walks themselves only bound blocks); with this flag each lane
+ * evaluates its own ray's leaf samples inside its walk.  Same results bit for
+ * bit. */
 #define SS_FLAG_LANE_LEAVES 0x10u
 
 /* Bits of the device status word (ss_outputs.status, ss_shadow_backward_ws). */
@@ -155,8 +156,9 @@ typedef struct {
                               stepping 16)                                     */
     int32_t refill_min;    /* forward kernels: a warp's idle lanes take new
                               rays once at least this many are idle, in
-                              [0, 32]; 0 = default (exact descent: 14 with
-                              leaf tasks, 10 in single-lane walks; else 6)     */
+                              [0, 32]; 0 = default (exact descent with leaf
+                              tasks: 14 on gnomonic, 22 on stereographic
+                              tiles; single-lane walks 10; else 6)             */
     int32_t ray_tile_w;    /* grid-mode rays: w > 0 = a block's rays form
                               rectangles of w x (rays / w) texels (w must
                               divide the block's or chunk's ray count);

@@ -250,14 +250,20 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
               : params->strip_len > 0 ? params->strip_len
               : light_only ? 1 : kDefaultStrip;
     a.seed_w = params->seed_width > 0 ? params->seed_width : (rays->mode == SS_RAYS_GRID ? 1 : 2);
-    // warp services: the task descent (exact walks with column seeds on gnomonic
-    // tiles, see ss_forward.cuh) waits for 14 idle lanes, the single-lane walk
-    // for 10 (sweeps over sun directions and chunk shapes on the 4096^2 tile)
-    const bool tasks = descent && !light_only && hf->projection == SS_PROJ_GNOMONIC &&
-                       a.colseed && !(params->flags & SS_FLAG_LANE_LEAVES) &&
-                       a.kleaf <= (rays->mode == SS_RAYS_GRID ? 1 : 2) &&
+    // warp services: the task descent (exact walks with column seeds, see
+    // ss_forward.cuh) waits for 14 idle lanes on gnomonic tiles and 22 on
+    // stereographic ones, the single-lane walk for 10 (sweeps over sun
+    // directions and chunk shapes on the 4096^2 tile, and over 6-22 on the
+    // polar view at 8192^2 and 16384^2)
+    const bool grid_gn = rays->mode == SS_RAYS_GRID && hf->projection == SS_PROJ_GNOMONIC;
+    const bool tasks = descent && !light_only && a.colseed &&
+                       !(params->flags & SS_FLAG_LANE_LEAVES) && a.kleaf <= (grid_gn ? 1 : 2) &&
                        (rays->mode != SS_RAYS_GRID || a.tile_w > 0);
-    a.refill_min = params->refill_min > 0 ? params->refill_min : (tasks ? 14 : descent ? 10 : 6);
+    const bool stereo = hf->projection != SS_PROJ_GNOMONIC;
+    a.refill_min = params->refill_min > 0 ? params->refill_min
+                   : tasks                ? (stereo ? 22 : 14)
+                   : descent              ? 10
+                                          : 6;
     cudaError_t e = kind == FwdKind::Descent
                         ? ss::launch_dp_forward(a, block, (cudaStream_t)stream)
                         : ss::launch_uniform_forward(a, block, (cudaStream_t)stream);

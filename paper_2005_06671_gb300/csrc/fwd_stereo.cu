@@ -1,5 +1,6 @@
 // Forward kernels for polar stereographic tiles.
 #include "ss_forward.cuh"
+#include "ss_task.cuh"
 
 namespace ss {
 

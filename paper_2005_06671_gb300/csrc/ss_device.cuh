@@ -17,6 +17,9 @@
 // descent and the uniform kernel, so both see bit-identical sample values.
 #pragma once
 
+#ifdef SS_RANGE_CHECK
+#include <cstdio>
+#endif
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -628,6 +631,10 @@ __device__ __forceinline__ bool inside64(const Tile& T, const Geom64& G, int32_t
     return U >= 0.0 && U <= (double)(T.nx - 1) && V >= 0.0 && V <= (double)(T.ny - 1);
 }
 
+#ifdef SS_RANGE_CHECK
+static __device__ unsigned int g_range_mismatch, g_range_reentry;
+#endif
+
 // Polar stereographic usable range: the first run of in-tile samples.  The
 // ray's directions sweep a great circle (plane N . n = 0, N = p x s); the
 // preimage of a tile edge X = X_B is the small circle E . n = e0 with
@@ -698,6 +705,9 @@ static __device__ __noinline__ void sample_range_stereo(const Tile& T, const Geo
     // split the run: both samples are in the tile).
     const double tmax = (double)T.J * T.delta;
     int32_t run_lo = -1, run_hi = -1;
+#ifdef SS_RANGE_CHECK
+    bool run_ended = false;
+#endif
     double lo_t = 0.0;
     for (int i = 0; i <= nc; ++i) {
         const double hi_t = i < nc ? fmin(tc[i], tmax) : tmax;
@@ -711,10 +721,23 @@ static __device__ __noinline__ void sample_range_stereo(const Tile& T, const Geo
                             V <= (double)(T.ny - 1);
             if (lo <= hi) {
                 if (in) {
+#ifdef SS_RANGE_CHECK
+                    if (run_ended) {   // test builds: samples in the tile after the run
+                        const unsigned k = atomicAdd(&g_range_reentry, 1u);
+                        if (k < 8u || (k & (k - 1u)) == 0u)
+                            printf("re-entry %u up=%.9g vp=%.9g run [%d,%d] again at %d\n", k + 1u,
+                                   G.up, G.vp, run_lo, run_hi, lo);
+                        break;
+                    }
+#endif
                     if (run_lo < 0) run_lo = lo;
                     run_hi = hi;
                 } else if (run_lo >= 0) {
+#ifdef SS_RANGE_CHECK
+                    run_ended = true;   // (test builds look on for a re-entry)
+#else
                     break;
+#endif
                 }
             }
         }
@@ -741,6 +764,11 @@ static __device__ __noinline__ void sample_range_stereo(const Tile& T, const Geo
     j_hi = hi;
 }
 
+
+static __device__ __noinline__ bool sample_range_stereo_f32(const Tile& T, const Geom64& G,
+                                                         const RayF& r, int32_t& j_lo,
+                                                         int32_t& j_hi);
+
 template <bool kStereo>
 __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double href,
                                           float span, RayF& r) {
@@ -763,11 +791,24 @@ __device__ __forceinline__ void make_rayf(const Tile& T, const Geom64& G, double
         sample_range(T, G, r.j_lo, r.j_hi);
         r.bu = r.bv = r.inv8r = 0.0f;
     } else {
-        sample_range_stereo(T, G, r.j_lo, r.j_hi);
         r.b = (float)G.inv_a0;
         r.bu = (float)G.Bu;
         r.bv = (float)G.Bv;
         r.inv8r = (float)(G.nz_cross * T.g / (16.0 * T.R));
+        r.au = __fadd_rn(r.au_hi, r.au_lo);
+        r.av = __fadd_rn(r.av_hi, r.av_lo);
+        if (!sample_range_stereo_f32(T, G, r, r.j_lo, r.j_hi))
+            sample_range_stereo(T, G, r.j_lo, r.j_hi);
+#ifdef SS_RANGE_CHECK
+        {   // test builds: the float32 search against the FP64 one
+            int32_t a = 1, b = 0;
+            sample_range_stereo(T, G, a, b);
+            if ((a <= b || r.j_lo <= r.j_hi) && (a != r.j_lo || b != r.j_hi) &&
+                atomicAdd(&g_range_mismatch, 1u) < 8u)
+                printf("range mismatch up=%.9g vp=%.9g f32 [%d,%d] fp64 [%d,%d]\n", G.up, G.vp,
+                       r.j_lo, r.j_hi, a, b);
+        }
+#endif
     }
     r.au = __fadd_rn(r.au_hi, r.au_lo);
     r.av = __fadd_rn(r.av_hi, r.av_lo);
@@ -932,6 +973,94 @@ __device__ __forceinline__ void block_end(const Tile& T, const RayF& r, float jf
         u = __fmaf_rn(__fmaf_rn(jf, au, -__fmul_rn(w, r.bu)), id, r.u0);
         v = __fmaf_rn(__fmaf_rn(jf, av, -__fmul_rn(w, r.bv)), id, r.v0);
     }
+}
+
+// ------------------------------------------- stereographic range, float32
+// The first run of in-tile samples (what sample_range_stereo finds with FP64
+// crossings) from float32 positions, certified so that the result is the same:
+//  * a sample whose float32 position (block_end, exact-formula rise) is more
+//    than E inside every edge is inside, more than E outside an edge is
+//    outside; E is the walk's footprint margin taken at j = J (a bound of the
+//    float32 position error over the whole ray) plus the rounding of the
+//    margin itself;
+//  * the ray's image is a circle arc of radius rc = 1/(8 inv8r) texels, and the
+//    samples between two samples lie on the arc between them, within
+//    L^2/(4 rc) of its chord (length L, L < rc); the chord is as far inside
+//    the tile as its nearer end, so when both ends are inside by more than
+//    E + L^2/(4 rc) every sample between them is inside (certified).
+// A bisection keeps jl, the last sample known to continue the run from sample
+// 1, and jh, a sample the certificate does not reach from jl; at jh = jl + 1
+// sample jh is classified alone (FP64 when within E of an edge): outside ends
+// the run, inside starts another pass from it.  Returns false (the caller
+// runs the FP64 search) when sample 1 is not inside or after kRangePasses
+// passes (rays that run along an edge).
+constexpr int kRangePasses = 4;
+
+struct RangePt {
+    float u, v, m;   // float32 position, distance inside the nearest edge
+};
+
+__device__ __forceinline__ RangePt range_pt(const Tile& T, const RayF& r, int32_t j) {
+    RangePt p;
+    const float jf = (float)j;
+    const float t = __fmul_rn(jf, T.delta_f);
+    block_end<true>(T, r, jf, t, rise_of<false>(r, t), p.u, p.v);
+    p.m = fminf(fminf(p.u, (float)(T.nx - 1) - p.u), fminf(p.v, (float)(T.ny - 1) - p.v));
+    return p;
+}
+
+__device__ __forceinline__ bool range_cert(const RayF& r, const RangePt& a, const RangePt& b,
+                                           float E) {
+    const float du = b.u - a.u, dv = b.v - a.v;
+    const float L = sqrtf(du * du + dv * dv) + 3.0f * E;   // exact chord length bound
+    if (L * r.inv8r >= 0.125f) return false;               // chord not shorter than rc
+    const float sag = 2.02f * r.inv8r * L * L;             // L^2 / (4 rc), 1% margin
+    return fminf(a.m, b.m) - sag > E;
+}
+
+static __device__ __noinline__ bool sample_range_stereo_f32(const Tile& T, const Geom64& G,
+                                                         const RayF& r, int32_t& j_lo,
+                                                         int32_t& j_hi) {
+    const int32_t J = T.J;
+    if (J < 1) return false;
+    const float amax = fmaxf(fabsf(r.au), fabsf(r.av)), bmax = fmaxf(fabsf(r.bu), fabsf(r.bv));
+    const float E = 2e-3f + 5e-7f * (float)(T.nx + T.ny) + 8e-7f * amax * (float)J +
+                    8e-7f * bmax * 2.0f * ((float)J * T.delta_f);
+    RangePt pl = range_pt(T, r, 1);
+    if (!(pl.m > E) && (pl.m < -E || !inside64(T, G, 1))) return false;
+    int32_t jl = 1;
+    for (int pass = 0; pass < kRangePasses; ++pass) {
+        if (jl == J) break;
+        int32_t jh = J;
+        RangePt ph = range_pt(T, r, J);
+        if (range_cert(r, pl, ph, E)) {
+            jl = J;
+            break;
+        }
+        while (jh - jl > 1) {
+            const int32_t jm = jl + ((jh - jl) >> 1);
+            const RangePt pm = range_pt(T, r, jm);
+            if (range_cert(r, pl, pm, E)) {
+                jl = jm;
+                pl = pm;
+            } else {
+                jh = jm;
+                ph = pm;
+            }
+        }
+        const bool in = ph.m > E ? true : ph.m < -E ? false : inside64(T, G, jh);
+        if (!in) {
+            j_lo = 1;
+            j_hi = jl;
+            return true;
+        }
+        jl = jh;
+        pl = ph;
+    }
+    if (jl != J) return false;
+    j_lo = 1;
+    j_hi = J;
+    return true;
 }
 
 // Levels of the maximum mipmap as a kernel sees them (shared memory copy).

@@ -498,21 +498,22 @@ static cudaError_t dispatch(const FwdArgs& a, int block, cudaStream_t s) {
 template <bool kCount, bool kGrid, bool kPoly, bool kStereo>
 __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_task_kernel(const FwdArgs a);
 
-// The task descent (ss_task.cuh) serves exact walks with column seeds on
-// gnomonic tiles: grid rays in rectangles (leaf blocks of <= 4 samples),
-// listed rays in runs (<= 8).  Stereographic tiles keep the single-lane walk:
-// their FP64 ray setup, run by the few lanes a service refills, outweighs what
-// the tasks save (polar view, 6.0 M rays: 70 ms against 65 ms).
+// The task descent (ss_task.cuh) serves exact walks with column seeds: grid
+// rays in rectangles (leaf blocks of <= 4 samples on gnomonic tiles, <= 8 on
+// stereographic ones), listed rays in runs (<= 8).  (Polar view, 6.0 M rays on
+// the 16384^2 stereographic tile: 28.5 ms against 37.5 ms for the single-lane
+// walk, once the float32 range search took the FP64 crossings out of the
+// setup; with them the tasks had measured slower, 70 against 65 ms.)
 inline bool use_task_descent(const FwdArgs& a, bool grid, bool stereo, bool light) {
-    return !light && !stereo && a.colseed && (!grid || a.tile_w > 0) &&
-           a.kleaf <= (grid ? 1 : 2) && !(a.flags & 0x10u);   // SS_FLAG_LANE_LEAVES
+    return !light && a.colseed && (!grid || a.tile_w > 0) &&
+           a.kleaf <= (grid && !stereo ? 1 : 2) && !(a.flags & 0x10u);   // SS_FLAG_LANE_LEAVES
 }
 
 template <bool C, bool G, bool P, bool L, bool S>
 struct DpLaunch {
     static cudaError_t go(const FwdArgs& a, int grid, int block, cudaStream_t s) {
         bool tasks = false;
-        if constexpr (!S && !L) {   // defined for gnomonic tiles only (fwd_gnomonic.cu)
+        if constexpr (!L) {
             if (use_task_descent(a, G, S, L)) {
                 dp_task_kernel<C, G, P, S><<<grid, block, 0, s>>>(a);
                 tasks = true;

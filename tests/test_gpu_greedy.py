@@ -122,11 +122,18 @@ def test_float32_build_against_fp64_build(name, n, uv_n):
         assert agree.mean() > 0.97, agree.mean()
         ed, ef = np.abs(d["light"] - exact).mean(), np.abs(f["light"] - exact).mean()
         assert abs(ef - ed) <= 0.05 * ed + 1e-3, (ed, ef)
-        # in the penumbra the light fixes the cost: where the lights agree there,
-        # so do the costs (a saturated light says nothing about its cost)
-        pen = agree & (d["light"] > 0) & (d["light"] < 1) & (d["t_star"] > 0)
+        # inside the penumbra the light fixes the cost: where the lights agree
+        # there, so do the costs.  Near either end of the penumbra the visible
+        # disc fraction F(d) is flat (F'(d) = 2 sqrt(1 - d^2)/pi -> 0), so a light
+        # agreement of 1e-4 says little about the cost; lights in (0.02, 0.98)
+        # have F' > 0.1 and pin d to 1e-3, i.e. the cost to ~5e-6 rad.
+        pen = (agree & (d["light"] > 0.02) & (d["light"] < 0.98) & (f["light"] > 0.02)
+               & (f["light"] < 0.98) & (d["t_star"] > 0))
         assert pen.sum() > 20
-        assert np.all(np.abs(f["cost"][pen] - d["cost"][pen]) <= 2e-3 * np.abs(d["cost"][pen]) + 2e-5)
+        dc = np.abs(f["cost"][pen] - d["cost"][pen])
+        bar = 2e-3 * np.abs(d["cost"][pen]) + 2e-5
+        i = int(np.argmax(dc - bar))
+        assert np.all(dc <= bar), (dc[i], bar[i], d["light"][pen][i], f["light"][pen][i])
 
 
 def test_float32_build_rejects_stereographic_tiles():

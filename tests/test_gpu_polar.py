@@ -84,6 +84,44 @@ def test_wide_polar_tiles_vs_oracle_and_uniform(n, g, lmax, elev, az):
                       a["cost"][ids], ray_ids=ids, proj=PROJ)
 
 
+@pytest.mark.parametrize("n,g,lmax,elev,az,kw", [
+    (512, 300.0, 200e3, 1.0, 30.0, dict()),
+    (384, 1000.0, 400e3, 2.5, 200.0, dict(refill_min=1, leaf_level=0)),
+    (300, 600.0, 250e3, -0.3, 115.0, dict(refill_min=32, rays_per_thread=7, ray_tile_w=32)),
+    (257, 400.0, 150e3, 1.2, 250.0, dict(block_threads=96, rays_per_thread=3, ray_tile_w=16)),
+    (200, 500.0, 200e3, 0.7, 330.0, dict(leaf_level=2, count_samples=True)),
+])
+def test_polar_task_descent_equals_lane_descent(n, g, lmax, elev, az, kw):
+    """The default exact descent on stereographic tiles (leaf samples as
+    warp-wide tasks) against the single-lane walk (SS_FLAG_LANE_LEAVES) and
+    uniform stepping, bit for bit: grid rays over launch shapes (leaf blocks of
+    1, 4 and 8 samples, eager and lazy refills, partial warps, narrow and wide
+    ray rectangles) and listed rays inside and outside the tile, with lifts."""
+    h = _wide(n, g, seed=int(g) + 3 * n)
+    hf = ss.Heightfield(_dev(h), g, R, projection=PROJ)
+    mip = ss.ss_build_maxmip(hf)
+    sun = ss.Sun(math.radians(elev), math.radians(az), math.radians(0.2665))
+    rng = np.random.default_rng(n)
+    uv = np.concatenate([random_origins(3000, n, n, seed=n + 1),
+                         rng.uniform(-40, n + 40, (600, 2))]).astype(np.float32)
+    lift = rng.uniform(0, 200, uv.shape[0]).astype(np.float32)
+    lift[:1000] = 0.0
+    for rays in (dict(), dict(uv=_dev(uv), lift=_dev(lift))):
+        a = ss.ss_shadow_forward(hf, mip, sun, lmax, **rays, **kw)
+        b = ss.ss_shadow_forward(hf, mip, sun, lmax, lane_leaves=True, **rays, **kw)
+        u = ss.ss_shadow_uniform(hf, mip, sun, lmax, **rays)
+        torch.cuda.synchronize()
+        for x in (b, u):
+            assert torch.equal(a["argmin"], x["argmin"])
+            assert torch.equal(a["cost"].view(torch.int32), x["cost"].view(torch.int32))
+            assert torch.equal(a["light"].view(torch.int32), x["light"].view(torch.int32))
+        pen = ((a["light"] > 0) & (a["light"] < 1)).sum().item()
+        assert pen > 20
+        if kw.get("count_samples"):
+            ca = a["counters"].sum(0).cpu().numpy()
+            assert ca[0] > 0 and ca[1] > 0
+
+
 def test_polar_list_mode_inside_and_outside_origins():
     n, g, lmax = 257, 400.0, 150e3
     h = _wide(n, g, seed=91)
