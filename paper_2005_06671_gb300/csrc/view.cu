@@ -7,17 +7,18 @@
 //   d = unit(forward + a right + b up), x(tau) = C + tau d, samples tau_k = k step;
 //   the hit is the first sample whose texel image is in the tile and lies on or
 //   below the terrain (|x| - R - h <= 0, decided in FP64); when the sample
-//   before it is in the tile too the crossing is refined in FP64 by bisection
-//   to a bracket of 2^-36 of the step (see below_fast).
+//   before it is in the tile too the crossing is refined in FP64: bisection
+//   until the bracket lies in one bilinear cell, then the single root of the
+//   quadratic F there (see refine_crossing).
 // Sample blocks are walked near-to-far like the shadow descent (aligned blocks
 // of 2^k samples, next block at s0 += 2^k) in float32: a block is skipped when
 // the ray's lowest height over it exceeds the maximum-mipmap value over its
 // texel footprint by more than the float32 rounding, or when the footprint
 // misses the tile; a sample is tested in FP64 unless float32 shows it clearly
-// above the terrain or off the tile.  So the first sample found below the
-// terrain is the first one overall, the same sample as an FP64 march.
+// above or below the terrain or off the tile.  So the first sample found below
+// the terrain is the first one overall, the same sample as an FP64 march.
 //
-// A second pass gathers each block's hits and bisects them with full warps.
+// A second pass gathers each block's hits and refines them with full warps.
 // Then the hits are compacted in pixel order (per-block counts, one scan block,
 // a scatter), so the ray list is deterministic.
 #include <cuda_runtime.h>
@@ -32,7 +33,6 @@ namespace {
 
 constexpr int kViewBlock = 256;
 constexpr int kViewLeaf = 2;          // blocks of <= 4 samples are tested sample by sample
-constexpr double kViewGuard = 1e-3;   // m: FP64 rounding of heights and bounds is ~1e-9 m
 
 struct Cam {
     double C[3], f[3], r[3], u[3];
@@ -97,6 +97,51 @@ __device__ __forceinline__ bool below_fast(const Tile& T, const double C[3], con
     double w[4];
     const double hb = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, u, v, &i0, &j0, w);
     return (m - T.R) - hb <= 0.0;
+}
+
+// below_fast's arithmetic, keeping the value F = (|x| - R) - h and the texel
+// image: below_fast(tau) == (in && f <= 0), bit for bit.
+struct ViewPt {
+    double tau, f, u, v;
+    bool in;
+};
+
+__device__ __forceinline__ ViewPt view_pt(const Tile& T, const double C[3], const double d[3],
+                                          double tau) {
+    ViewPt p;
+    p.tau = tau;
+    p.f = 0.0;
+    p.u = p.v = 0.0;
+    p.in = false;
+    const double x[3] = { C[0] + tau * d[0], C[1] + tau * d[1], C[2] + tau * d[2] };
+    const double m = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    double k;
+    if (T.proj == 0) {
+        if (!(x[2] > 0.0)) return p;
+        k = (T.R * T.inv_g) / x[2];
+    } else {
+        const double den = m + x[2];
+        if (!(den > 0.0)) return p;
+        k = (2.0 * T.R * T.inv_g) / den;
+    }
+    p.u = x[0] * k + T.cx;
+    p.v = x[1] * k + T.cy;
+    if (!in_tile64(T, p.u, p.v)) return p;
+    p.in = true;
+    int32_t i0, j0;
+    double w[4];
+    const double hb = fetch_bilinear64(T.h, T.pitch, T.nx, T.ny, p.u, p.v, &i0, &j0, w);
+    p.f = (m - T.R) - hb;
+    return p;
+}
+
+// the bilinear cell fetch_bilinear64 reads for in-tile point p
+__device__ __forceinline__ bool same_cell(const Tile& T, const ViewPt& a, const ViewPt& b) {
+    const int32_t ia = min(max((int32_t)floor(a.u), 0), T.nx - 2);
+    const int32_t ib = min(max((int32_t)floor(b.u), 0), T.nx - 2);
+    const int32_t ja = min(max((int32_t)floor(a.v), 0), T.ny - 2);
+    const int32_t jb = min(max((int32_t)floor(b.v), 0), T.ny - 2);
+    return ia == ib && ja == jb;
 }
 
 // maximum of the heights over texel box [x0, x1] x [y0, y1] (inclusive, clamped
@@ -216,8 +261,9 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
         // the maximum height under its footprint by more than kBlockGuard (the
         // rounding of the float32 height is ~1e-2 m); a sample is ruled out
         // when it is above the bilinear terrain by more than kLeafGuard plus a
-        // share of its cell's height range (position error <= 2e-3 texel);
-        // anything closer is decided in FP64 (below()), as before.
+        // share of its cell's height range (position error <= 2e-3 texel), and
+        // is a hit when it is below by as much; anything closer is decided in
+        // FP64 (below()), as before.
         constexpr float kBlockGuard = 0.05f, kLeafGuard = 0.05f, kPosMargin = 0.01f;
         const float nxm = (float)(T.nx - 1), nym = (float)(T.ny - 1);
         if (k0 <= k1) {
@@ -236,6 +282,7 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
                         const float rs = rise_of<false>(q.rise, t);
                         float u, v;
                         bool decide = true;   // false: certainly no hit at this sample
+                        bool hit = false;     // certainly a hit (below by more than the guard)
                         if (view_image_f(T, q, t, rs, u, v)) {
                             const bool out = u < -kPosMargin || u > nxm + kPosMargin ||
                                              v < -kPosMargin || v > nym + kPosMargin;
@@ -255,8 +302,14 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
                                 const float hb = top + fv * (bot - top);
                                 const float rng = fmaxf(fmaxf(h00, h10), fmaxf(h01, h11)) -
                                                   fminf(fminf(h00, h10), fminf(h01, h11));
-                                decide = !((q.alt + rs) - hb > kLeafGuard + 0.01f * rng);
+                                const float gap = (q.alt + rs) - hb, gd = kLeafGuard + 0.01f * rng;
+                                decide = !(gap > gd);
+                                hit = gap < -gd;
                             }
+                        }
+                        if (hit) {
+                            hit_k = qj;
+                            break;
                         }
                         if (decide) {
                             bool ins;
@@ -304,6 +357,104 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
     }
 }
 
+// The crossing of F in [lo, hi] (F(lo) > 0 in the tile, F(hi) <= 0): the upper
+// end of a bracket of the crossing.  The halvings of the bisection run until
+// both ends lie in one bilinear cell: up to there the choices are the
+// bisection's own (below_fast's arithmetic).  Inside one cell the terrain
+// along the ray is a quadratic in tau (bilinear along a line; the image arc
+// bends by ~1e-8 texel over a cell) and so is the ray's height (to ~1e-12 m),
+// so F has exactly one root in a bracket where it changes sign: F at the
+// midpoint and the quadratic through the three values place it, and one more
+// value confirms a bracket [r - eps, r] or [r, r + eps] around the estimate r,
+// eps = 8 x the FP64 rounding of F (2e-9 m) over the slope |F'| (at least
+// 2^-36 of the step, the bisection's own bracket).  The upper end then lies
+// within eps of the crossing, below 1/3 of a float32 step of texel
+// coordinates >= 0.25.  Near-tangent crossings (eps above 2^-22 of the step),
+// points near the tile's low edges and failed confirmations finish with
+// halvings to 2^-kViewHalvings of the step, as before.
+__device__ __noinline__ double refine_crossing(const Tile& T, const double C[3], const double d[3],
+                                               double lo_t, double hi_t, double step) {
+    ViewPt lo = view_pt(T, C, d, lo_t), hi = view_pt(T, C, d, hi_t);
+    const double tol = ldexp(step, -kViewHalvings);
+    if (!(lo.in && lo.f > 0.0 && hi.in && hi.f <= 0.0)) {
+        // (below()'s and below_fast's roundings disagree at an end): plain halvings
+        for (int it = 0; it < kViewHalvings; ++it) {
+            const double mid = lo_t + 0.5 * (hi_t - lo_t);
+            if (below_fast(T, C, d, mid))
+                hi_t = mid;
+            else
+                lo_t = mid;
+        }
+        return hi_t;
+    }
+    int it = 0;
+    for (; it < kViewHalvings && !same_cell(T, lo, hi); ++it) {
+        const ViewPt m = view_pt(T, C, d, lo.tau + 0.5 * (hi.tau - lo.tau));
+        if (m.in && m.f <= 0.0)
+            hi = m;
+        else
+            lo = m;
+        if (!lo.in) break;   // (the ray left the tile between samples)
+    }
+    if (it < kViewHalvings && lo.in && same_cell(T, lo, hi)) {
+        const double t0 = lo.tau, h = hi.tau - lo.tau;
+        const ViewPt m = view_pt(T, C, d, t0 + 0.5 * h);
+        // quadratic F(t0 + s h) = A + B s + Cq s^2 through s = 0, 1/2, 1
+        const double A = lo.f, Cq = 2.0 * (lo.f + hi.f - 2.0 * m.f), B = hi.f - lo.f - Cq;
+        if (m.in && same_cell(T, lo, m)) {
+            if (m.f <= 0.0)
+                hi = m;
+            else
+                lo = m;
+        }
+        const double l0 = (lo.tau - t0) / h, l1 = (hi.tau - t0) / h;   // bracket in s
+        double s = -1.0;
+        if (fabs(Cq) <= 1e-12 * fabs(B)) {
+            if (B != 0.0) s = -A / B;
+        } else {
+            const double disc = B * B - 4.0 * A * Cq;
+            if (disc >= 0.0) {
+                const double q = -0.5 * (B + copysign(sqrt(disc), B));
+                const double s1 = q / Cq, s2 = q != 0.0 ? A / q : -1.0;
+                s = (s1 >= l0 && s1 <= l1) ? s1 : s2;
+            }
+        }
+        const double r = t0 + s * h;
+        const double slope = fabs((B + 2.0 * Cq * s) / h);
+        const double eps = fmax(tol, 1.6e-8 / slope);
+        const bool low_edge = fmin(lo.u, lo.v) < 0.25 || fmin(hi.u, hi.v) < 0.25;
+        if (s >= l0 && s <= l1 && r > lo.tau && r <= hi.tau && slope > 0.0 &&
+            eps <= ldexp(step, -22) && !low_edge) {
+            const ViewPt pr = view_pt(T, C, d, r);
+            if (pr.in && same_cell(T, lo, pr)) {
+                if (pr.f <= 0.0) {           // crossing in (lo, r]
+                    hi = pr;
+                    if (r - eps <= lo.tau) return hi.tau;
+                    const ViewPt pc = view_pt(T, C, d, r - eps);
+                    if (pc.in && pc.f > 0.0) return hi.tau;
+                    if (pc.in) hi = pc;
+                } else {                     // crossing in (r, hi]
+                    lo = pr;
+                    if (r + eps >= hi.tau) return hi.tau;
+                    const ViewPt pc = view_pt(T, C, d, r + eps);
+                    if (pc.in && pc.f <= 0.0) return pc.tau;
+                    if (pc.in) lo = pc;
+                }
+            }
+        }
+    }
+    // halvings of whatever bracket is left, down to the bisection's resolution
+    double a_t = lo.tau, b_t = hi.tau;
+    for (int k = 0; k < 2 * kViewHalvings && b_t - a_t > tol; ++k) {
+        const double mid = a_t + 0.5 * (b_t - a_t);
+        if (below_fast(T, C, d, mid))
+            b_t = mid;
+        else
+            a_t = mid;
+    }
+    return b_t;
+}
+
 // Pass 2: the hits of a block of pixels, gathered in shared memory so that
 // full warps run the FP64 bisection of the crossing (a pass-1 warp has a hit in
 // only some of its lanes); writes every pixel's texel coordinates (NaN without
@@ -335,16 +486,7 @@ __global__ void __launch_bounds__(kViewBlock) view_refine_kernel(const ViewArgs 
             double u, v;
             below(T, C, d, (double)(hit_k - 1) * a.step, prev_in, u, v);
         }
-        if (prev_in) {
-            double lo = (double)(hit_k - 1) * a.step;
-            for (int it = 0; it < kViewHalvings; ++it) {
-                const double mid = lo + 0.5 * (hi - lo);
-                if (below_fast(T, C, d, mid))
-                    hi = mid;
-                else
-                    lo = mid;
-            }
-        }
+        if (prev_in) hi = refine_crossing(T, C, d, (double)(hit_k - 1) * a.step, hi, a.step);
         const double xh[3] = { C[0] + hi * d[0], C[1] + hi * d[1], C[2] + hi * d[2] };
         double hu, hv;
         // the point lies between two samples of the tile: it has an image
