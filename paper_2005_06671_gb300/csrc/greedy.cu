@@ -175,6 +175,47 @@ __device__ float run_length_f32(const Tile& T, const float rs[3], const float s[
     return (ce[0] * se[0] + ce[1] * se[1] + ce[2] * se[2]) / den;
 }
 
+// A tip the float32 margin leaves ambiguous, for grid rays: its texel image
+// u = u_p + Au j/(1 + b j), j = dist/delta, in float-float (relative error
+// ~1e-13, ~1e-9 texel), the same map geom64 evaluates in FP64.  Returns false
+// (FP64 decides) when the position is within 1e-6 texel of a tile edge or of
+// the cell edge that decides the mip texel.
+__device__ __forceinline__ bool tip_df(const Tile& T, const RayF& rf, float dist, float cell,
+                                       int32_t w, int32_t h, bool& have, DF A[3], bool& in,
+                                       int32_t& I, int32_t& J) {
+    if (!have) {
+        gnomonic_grid_df(T, rf.u0, rf.v0, rf.href, A[0], A[1], A[2]);
+        have = true;
+    }
+    const DF jd = df_div(DF{ dist, 0.0f }, DF{ T.delta_hi, T.delta_lo });
+    const DF den = df_add(DF{ 1.0f, 0.0f }, df_mul(A[2], jd));
+    if (!(den.hi > 0.25f)) return false;   // (far along the ray: FP64 decides)
+    const DF tau = df_div(jd, den);
+    const DF U = df_add(DF{ rf.u0, 0.0f }, df_mul(A[0], tau));
+    const DF V = df_add(DF{ rf.v0, 0.0f }, df_mul(A[1], tau));
+    // every decision is the sign of a float-float difference: hi may be an
+    // integer (or an edge) exactly while lo carries the other side
+    constexpr float kE2 = 1e-6f;
+    const float lim[4] = { 0.0f, (float)(T.nx - 1), 0.0f, (float)(T.ny - 1) };
+    float d[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        d[e] = df_add(e < 2 ? U : V, DF{ -lim[e], 0.0f }).hi;
+        if (fabsf(d[e]) < kE2) return false;
+    }
+    in = d[0] > 0.0f && d[1] < 0.0f && d[2] > 0.0f && d[3] < 0.0f;
+    const float ic = 1.0f / cell;   // a power of two: exact scaling
+    const DF fu = df_add(U, DF{ 0.5f, 0.0f }), fv = df_add(V, DF{ 0.5f, 0.0f });
+    const DF su = { fu.hi * ic, fu.lo * ic }, sv = { fv.hi * ic, fv.lo * ic };
+    const float nu = rintf(su.hi), nv = rintf(sv.hi);
+    const float du = df_add(su, DF{ -nu, 0.0f }).hi, dv = df_add(sv, DF{ -nv, 0.0f }).hi;
+    if (fabsf(du) < kE2 * ic || fabsf(dv) < kE2 * ic) return false;
+    // floor(x) = n - 1 below the nearest integer n, n above it
+    I = min(max((int32_t)nu - (du < 0.0f ? 1 : 0), 0), w - 1);
+    J = min(max((int32_t)nv - (dv < 0.0f ? 1 : 0), 0), h - 1);
+    return true;
+}
+
 template <bool kGrid>
 __global__ void __launch_bounds__(256) greedy_f32_kernel(const GreedyArgs a) {
     const Tile& T = a.T;
@@ -198,8 +239,9 @@ __global__ void __launch_bounds__(256) greedy_f32_kernel(const GreedyArgs a) {
         p0[0] = rho * Xp * im;
         p0[1] = rho * Yp * im;
         p0[2] = T.R_f * im * (hp - (Xp * Xp + Yp * Yp) / (m + T.R_f));
-        bool have64 = false;
+        bool have64 = false, have_df = false;
         double p64[3] = { 0.0, 0.0, 0.0 };
+        DF Adf[3];   // grid rays: float-float Au, Av, b (on the first ambiguous tip)
         const float amax = fmaxf(fabsf(rf.au), fabsf(rf.av));
         float bestJ = INFINITY, bestd = -1.0f, start = 0.0f;
         for (int32_t run = 0; run < a.n_runs; ++run) {
@@ -236,6 +278,8 @@ __global__ void __launch_bounds__(256) greedy_f32_kernel(const GreedyArgs a) {
                              v <= (float)(T.ny - 1);
                         I = min(max((int32_t)floorf(fu), 0), w - 1);
                         J = min(max((int32_t)floorf(fv), 0), h - 1);
+                    } else if (kGrid && tip_df(T, rf, dist, cell, w, h, have_df, Adf, in, I, J)) {
+                        // settled in float-float
                     } else {
                         if (!have64) {
                             double up, vp, hp, href, ow[4];

@@ -512,10 +512,10 @@ __device__ __forceinline__ void split8_df(DF a, float& hi, float& lo) {
 // m = |(X, Y, R)|, f = delta m / (R + h), a = f (R s_xy - s_z (X, Y)) / (g R),
 // b = f s_z / R), the exit sample from the float estimate; FP64 only when
 // that estimate is in doubt or the exit cannot be found that way.
-__device__ __forceinline__ void make_rayf_gnomonic_grid(const Tile& T, int32_t u, int32_t v,
-                                                        float h, float span, RayF& r,
-                                                        float& sin_e) {
-    const float uf = (float)u, vf = (float)v;
+// The gnomonic map of a grid ray from texel (u, v) at height h in float-float:
+// u_j = u + Au j/(1 + b j) (and v), as geom64 computes it in FP64.
+__device__ __forceinline__ void gnomonic_grid_df(const Tile& T, float uf, float vf, float h,
+                                                 DF& Au, DF& Av, DF& b) {
     const DF g = { T.g_hi, T.g_lo };
     const DF Xp = df_mul_f(g, __fsub_rn(uf, T.cx_f));   // u - cx exact (half-integers)
     const DF Yp = df_mul_f(g, __fsub_rn(vf, T.cy_f));
@@ -524,9 +524,17 @@ __device__ __forceinline__ void make_rayf_gnomonic_grid(const Tile& T, int32_t u
     const DF f = df_mul(DF{ T.delta_hi, T.delta_lo }, df_div(df_sqrt(m2), rho));
     const DF k = df_mul(f, DF{ T.igR_hi, T.igR_lo });
     const DF sz = { T.sz_f, T.sz_lo };
-    const DF Au = df_mul(k, df_add(DF{ T.Rsx_hi, T.Rsx_lo }, df_neg(df_mul(sz, Xp))));
-    const DF Av = df_mul(k, df_add(DF{ T.Rsy_hi, T.Rsy_lo }, df_neg(df_mul(sz, Yp))));
-    const DF b = df_mul_f(f, T.szR_f);
+    Au = df_mul(k, df_add(DF{ T.Rsx_hi, T.Rsx_lo }, df_neg(df_mul(sz, Xp))));
+    Av = df_mul(k, df_add(DF{ T.Rsy_hi, T.Rsy_lo }, df_neg(df_mul(sz, Yp))));
+    b = df_mul_f(f, T.szR_f);
+}
+
+__device__ __forceinline__ void make_rayf_gnomonic_grid(const Tile& T, int32_t u, int32_t v,
+                                                        float h, float span, RayF& r,
+                                                        float& sin_e) {
+    const float uf = (float)u, vf = (float)v;
+    DF Au, Av, b;
+    gnomonic_grid_df(T, uf, vf, h, Au, Av, b);
     const float Xf = (uf - T.cx_f) * T.g_f, Yf = (vf - T.cy_f) * T.g_f;
     const float imf = rsqrtf(Xf * Xf + Yf * Yf + T.R_f * T.R_f);
     const float se = (Xf * T.sx_f + Yf * T.sy_f + T.R_f * T.sz_f) * imf;
