@@ -72,7 +72,9 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_task_kernel(const F
     float best = INFINITY;
     while (true) {
         unsigned act = __ballot_sync(kFull, r >= 0 && !done);
-        const unsigned want = __ballot_sync(kFull, (r < 0 || done) && open);
+        // lanes that want a ray: the others, while the pool is open (open is
+        // warp-uniform: only draw_strip, run by every lane, changes it)
+        const unsigned want = open ? ~act : 0u;
         if (act == 0 || __popc(want) >= a.refill_min) {
             while (count > 0) task_pass<kGrid, kPoly, kStereo>(a.T, W, head, count, lane);
             if (done) {
