@@ -152,7 +152,7 @@ typedef struct {
                               rays and the batch 1, listed rays 2)             */
     int32_t rays_per_thread; /* forward kernels: a block owns block_threads x
                               rays_per_thread rays, in [0, 4096]; 0 = default
-                              (descent: grid rays 24, listed rays 32; uniform
+                              (descent: grid rays 24, listed rays 12; uniform
                               stepping 16)                                     */
     int32_t refill_min;    /* forward kernels: a warp's idle lanes take new
                               rays once at least this many are idle, in
@@ -439,10 +439,14 @@ ss_status ss_shade(const ss_heightfield* hf, const ss_rays* rays, const ss_light
  * floor(max_dist_m / step_m), are tested in order; the hit is the first one
  * whose texel image lies in [0,nx-1] x [0,ny-1] with |x| - R - h(image) <= 0
  * (h bilinear, decided in FP64); when the sample before it is in the tile too
- * the crossing is refined in FP64 by bisection of that step down to a bracket
- * of 2^-36 of it, finer than FP64 resolves |x| - R at a planetary radius (the
- * float32 coordinates equal those of a longer bisection).  The march itself
- * runs in float32 and defers to FP64 near the terrain and the tile's border.
+ * the crossing is refined in FP64: bisection of that step until the bracket
+ * lies in one bilinear cell, then the single root there of the quadratic that
+ * |x| - R - h is along the ray within one cell, placed within 8x the FP64
+ * rounding of that difference over its slope (within a third of a float32
+ * step of the texel coordinates; points within 0.25 texel of the tile's low
+ * edges, and near-tangent crossings, bisect on to 2^-36 of the step).  The
+ * march itself runs in float32 and defers to FP64 near the terrain and the
+ * tile's border.
  *
  * Output: the hits' texel coordinates (u, v) as float32 pairs in pixel order,
  * uv[2*r], uv[2*r+1] for r < *count (device int64 written by the call), and

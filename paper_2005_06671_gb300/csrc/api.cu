@@ -233,7 +233,7 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread
                         : !descent                     ? 16
                         : rays->mode == SS_RAYS_GRID   ? 24
-                                                       : 32;
+                                                       : 12;
     a.rays_per_block = (int64_t)block * rpt;
     a.poly = rise_series_ok(hf, sun, J * delta, rays->mode) ? 1 : 0;
     a.tile_w = params->ray_tile_w;
