@@ -23,6 +23,8 @@
 // a scatter), so the ray list is deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdint.h>
 
 #include "ss_launch.h"
@@ -38,13 +40,16 @@ struct Cam {
     double C[3], f[3], r[3], u[3];
     double tan_x, tan_y;
     int32_t W, H;
+    // per launch (host): 2/W, 2/H; |C|^2, |C|; the float32 ray state's camera terms
+    double inv_w2, inv_h2, cc, cn;
+    float cxf, cyf, czf, alt, zsum, inv_2cn, two_r_g;
 };
 
 struct ViewArgs {
     Tile T;
     Pyramid P;
     Cam cam;
-    double step;
+    double step, inv_step;
     int64_t K;
     const float* stats;       // (global max, global min) of the heights
     float2* pix_uv;           // per pixel: hit texel coords, NaN when none
@@ -197,13 +202,13 @@ __device__ __forceinline__ bool view_image_f(const Tile& T, const ViewRayF& q, f
 // unit direction of pixel pix's view ray
 __device__ __forceinline__ void pixel_dir(const Cam& cm, int64_t pix, double d[3]) {
     const int64_t i = pix % cm.W, j = pix / cm.W;
-    const double aa = (2.0 * ((double)i + 0.5) / (double)cm.W - 1.0) * cm.tan_x;
-    const double bb = (1.0 - 2.0 * ((double)j + 0.5) / (double)cm.H) * cm.tan_y;
+    const double aa = (((double)i + 0.5) * cm.inv_w2 - 1.0) * cm.tan_x;
+    const double bb = (1.0 - ((double)j + 0.5) * cm.inv_h2) * cm.tan_y;
 #pragma unroll
     for (int k = 0; k < 3; ++k) d[k] = cm.f[k] + aa * cm.r[k] + bb * cm.u[k];
-    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double idn = 1.0 / sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] /= dn;
+    for (int k = 0; k < 3; ++k) d[k] *= idn;
 }
 
 // Pass 1: per pixel, the first sample below the terrain (hit_k, -1 when none).
@@ -221,16 +226,16 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
         const double hmax = (double)a.stats[0];
         const double Rm = T.R + hmax;
         const double cd = C[0] * d[0] + C[1] * d[1] + C[2] * d[2];
-        const double cc = C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
-        const double disc = cd * cd - (cc - Rm * Rm);
+        const double disc = cd * cd - (cm.cc - Rm * Rm);
         int64_t k0 = 1, k1 = 0;
         if (disc >= 0.0) {
             const double sq = sqrt(disc);
             const double tau_in = -cd - sq, tau_out = -cd + sq;
             if (tau_out >= 0.0) {
-                k0 = tau_in > 0.0 ? (int64_t)floor(tau_in / a.step) - 1 : 1;
+                // (the one-sample margins cover the rounding of the reciprocal)
+                k0 = tau_in > 0.0 ? (int64_t)floor(tau_in * a.inv_step) - 1 : 1;
                 k0 = k0 < 1 ? 1 : k0;
-                k1 = (int64_t)ceil(tau_out / a.step) + 1;
+                k1 = (int64_t)ceil(tau_out * a.inv_step) + 1;
                 k1 = k1 > a.K ? a.K : k1;
             }
         }
@@ -243,18 +248,17 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
             inv8r = nn > 0.0 ? (float)(fabs(N[2]) / nn * T.g / (16.0 * T.R)) : 0.0f;
         }
         ViewRayF q;
-        const double cn = sqrt(cc);
-        q.cx = (float)C[0];
-        q.cy = (float)C[1];
-        q.cz = (float)(C[2] - T.R);
+        q.cx = cm.cxf;
+        q.cy = cm.cyf;
+        q.cz = cm.czf;
         q.dx = (float)d[0];
         q.dy = (float)d[1];
         q.dz = (float)d[2];
-        q.alt = (float)(cn - T.R);
-        q.two_r_g = (float)((T.proj == 0 ? 1.0 : 2.0) * T.R / T.g);
-        q.zsum = (float)(cn + T.R);
+        q.alt = cm.alt;
+        q.two_r_g = cm.two_r_g;
+        q.zsum = cm.zsum;
         q.rise.B = (float)(2.0 * cd);
-        q.rise.inv_2rho = (float)(0.5 / cn);
+        q.rise.inv_2rho = cm.inv_2cn;
         const float stepf = (float)a.step;
         const float tv = (float)(-cd);   // closest approach to the centre
         // float32 guards: a block is skipped when its lowest ray height is above
@@ -576,7 +580,19 @@ cudaError_t launch_view_rays(const Tile& T, const Pyramid& P, const ViewCamera& 
     a.cam.tan_y = vc.tan_y;
     a.cam.W = vc.width;
     a.cam.H = vc.height;
+    a.cam.inv_w2 = 2.0 / (double)vc.width;
+    a.cam.inv_h2 = 2.0 / (double)vc.height;
+    a.cam.cc = vc.pos[0] * vc.pos[0] + vc.pos[1] * vc.pos[1] + vc.pos[2] * vc.pos[2];
+    a.cam.cn = std::sqrt(a.cam.cc);
+    a.cam.cxf = (float)vc.pos[0];
+    a.cam.cyf = (float)vc.pos[1];
+    a.cam.czf = (float)(vc.pos[2] - T.R);
+    a.cam.alt = (float)(a.cam.cn - T.R);
+    a.cam.zsum = (float)(a.cam.cn + T.R);
+    a.cam.inv_2cn = (float)(0.5 / a.cam.cn);
+    a.cam.two_r_g = (float)((T.proj == 0 ? 1.0 : 2.0) * T.R / T.g);
     a.step = step;
+    a.inv_step = 1.0 / step;
     a.K = K;
     a.stats = stats;
     const int64_t npix = (int64_t)vc.width * vc.height, nb = view_blocks(vc.width, vc.height);
