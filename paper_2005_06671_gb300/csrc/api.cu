@@ -145,8 +145,11 @@ ss::Tile make_tile(const ss_heightfield* hf, const ss_sun* sun, int32_t J, doubl
     split(T.inv_gR, T.igR_hi, T.igR_lo);
     split(R * s[0], T.Rsx_hi, T.Rsx_lo);
     split(R * s[1], T.Rsy_hi, T.Rsy_lo);
-    float sz_hi;
+    float sz_hi, sx_hi, sy_hi;
     split(s[2], sz_hi, T.sz_lo);
+    split(s[0], sx_hi, T.sx_lo);
+    split(s[1], sy_hi, T.sy_lo);
+    split(2.0 * R / g, T.k2_hi, T.k2_lo);
     T.szR_f = (float)(s[2] / R);
     return T;
 }

@@ -60,6 +60,8 @@ struct Tile {
     // float-float (hi + lo) copies for the grid-ray setup (df_* below)
     float g_hi, g_lo, R_lo, RR_hi, RR_lo, delta_hi, delta_lo, igR_hi, igR_lo;
     float Rsx_hi, Rsx_lo, Rsy_hi, Rsy_lo, sz_lo, szR_f;
+    // and for the stereographic setup: sx, sy (low words), 2R/g
+    float sx_lo, sy_lo, k2_hi, k2_lo;
 };
 
 struct Rays {
@@ -449,6 +451,74 @@ __device__ __forceinline__ DF df_div(DF x, DF y) {
 }
 
 __device__ __forceinline__ double df_to_double(DF x) { return (double)x.hi + (double)x.lo; }
+
+// geom64_stereo's fields from float-float arithmetic (relative error ~1e-13
+// against its ~1e-16): the divisions, the square root and the products run on
+// the float32 pipes, and the FP64 values are assembled from the two words.
+// (u, v): origin texel coordinates (float); hp: origin height.
+__device__ __forceinline__ void geom_stereo_df(const Tile& T, float uf, float vf, DF hp,
+                                               Geom64& G) {
+    const DF g = { T.g_hi, T.g_lo };
+    const DF Xp = df_mul(g, df_two_sum(uf, -T.cx_f));
+    const DF Yp = df_mul(g, df_two_sum(vf, -T.cy_f));
+    const DF fr = { 4.0f * T.RR_hi, 4.0f * T.RR_lo };   // 4 R^2 (exact scaling)
+    const DF r2 = df_add(df_mul(Xp, Xp), df_mul(Yp, Yp));
+    const DF den = df_add(fr, r2);
+    const DF iden = df_div(DF{ 1.0f, 0.0f }, den);
+    const DF R4 = { 4.0f * T.R_f, 4.0f * T.R_lo };
+    const DF nx = df_mul(df_mul(R4, Xp), iden), ny = df_mul(df_mul(R4, Yp), iden);
+    const DF nz = df_mul(df_add(fr, df_neg(r2)), iden);
+    const DF sx = { T.sx_f, T.sx_lo }, sy = { T.sy_f, T.sy_lo }, sz = { T.sz_f, T.sz_lo };
+    const DF se = df_add(df_add(df_mul(nx, sx), df_mul(ny, sy)), df_mul(nz, sz));
+    const DF rho = df_add(DF{ T.R_f, T.R_lo }, hp);
+    const DF irho = df_div(DF{ 1.0f, 0.0f }, rho);
+    // a0 = rho (1 + n_z) = 2 fr rho / (fr + r2)
+    const DF ia0 = df_div(df_mul(irho, den), DF{ 2.0f * fr.hi, 2.0f * fr.lo });
+    const DF k2 = { T.k2_hi, T.k2_lo };
+    const DF dk = df_mul(DF{ T.delta_hi, T.delta_lo }, k2);
+    const DF kr = df_mul(df_mul(k2, rho), df_mul(ia0, ia0));
+    G.up = (double)uf;
+    G.vp = (double)vf;
+    G.hp = df_to_double(hp);
+    G.nhat[0] = df_to_double(nx);
+    G.nhat[1] = df_to_double(ny);
+    G.nhat[2] = df_to_double(nz);
+    G.sin_e = df_to_double(se);
+    G.rho = df_to_double(rho);
+    G.inv_rho = df_to_double(irho);
+    G.inv_a0 = df_to_double(ia0);
+    G.Au = df_to_double(df_mul(df_mul(dk, sx), ia0));
+    G.Av = df_to_double(df_mul(df_mul(dk, sy), ia0));
+    G.Bu = df_to_double(df_mul(kr, nx));
+    G.Bv = df_to_double(df_mul(kr, ny));
+    G.b = 0.0;
+    // |z of unit(n x s)| (image circle curvature; a float32 bound is enough)
+    const float cxf = ny.hi * sz.hi - nz.hi * sy.hi, cyf = nz.hi * sx.hi - nx.hi * sz.hi;
+    const float czf = nx.hi * sy.hi - ny.hi * sx.hi;
+    const float cnf = sqrtf(cxf * cxf + cyf * cyf + czf * czf);
+    G.nz_cross = cnf > 0.0f ? (double)(fabsf(czf) / cnf) : 0.0;
+}
+
+// Origin of listed ray r in float-float: the bilinear height at its (u, v)
+// (fetch_bilinear64's cell and weights) plus its lift; href = the cell's base
+// texel height.
+__device__ __forceinline__ DF origin_height_df(const Tile& T, float uf, float vf, float lift,
+                                               float& href) {
+    int32_t i0 = (int32_t)floorf(uf), j0 = (int32_t)floorf(vf);
+    i0 = min(max(i0, 0), T.nx - 2);
+    j0 = min(max(j0, 0), T.ny - 2);
+    const float fu = uf - (float)i0, fv = vf - (float)j0;   // exact
+    const DF gu = df_two_sum(1.0f, -fu), gv = df_two_sum(1.0f, -fv);
+    const float* p = T.h + (int64_t)j0 * T.pitch + i0;
+    const float h00 = p[0], h10 = p[1], h01 = p[T.pitch], h11 = p[T.pitch + 1];
+    DF acc = df_mul_f(df_mul(gu, gv), h00);
+    acc = df_add(acc, df_mul_f(df_mul(DF{ fu, 0.0f }, gv), h10));
+    acc = df_add(acc, df_mul_f(df_mul(gu, DF{ fv, 0.0f }), h01));
+    acc = df_add(acc, df_mul_f(DF{ __fmul_rn(fu, fv), __fmaf_rn(fu, fv, -__fmul_rn(fu, fv)) },
+                               h11));
+    href = h00;
+    return df_add(acc, DF{ lift, 0.0f });
+}
 
 // 1/rho^2 from 1/(2 rho) (gnomonic setup; recomputed when a parked ray is loaded)
 __device__ __forceinline__ float inv_rho2_of(float inv_2rho) {

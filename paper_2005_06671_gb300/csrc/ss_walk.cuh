@@ -121,21 +121,28 @@ __device__ __forceinline__ void setup_ray(const Tile& T, const Rays& R, int64_t 
         vp = (double)v;
         hp = href = (double)T.h[(int64_t)v * T.pitch + u];
     } else {
-        double ow[4];
-        int32_t oi0, oj0;
-        ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
         uf = R.uv[2 * r];
         vf = R.uv[2 * r + 1];
         if (R.status && !(isfinite(uf) && isfinite(vf) && (!R.lift || isfinite(R.lift[r]))))
             atomicOr(R.status, kDevNonfiniteRay);
+        if (!kStereo) {
+            double ow[4];
+            int32_t oi0, oj0;
+            ray_origin(T, R, r, up, vp, hp, href, oi0, oj0, ow);
+        }
     }
     float se;
     if (!kStereo) {
         make_rayf_gnomonic<kGrid>(T, up, vp, uf, vf, hp, href, span, rf, se);
     } else {
+        // origin and local frame in float-float (stereographic, see geom_stereo_df)
+        float hr;
+        const DF hpd = kGrid ? DF{ (float)hp, 0.0f }
+                             : origin_height_df(T, uf, vf, R.lift ? R.lift[r] : 0.0f, hr);
+        if (kGrid) hr = (float)href;
         Geom64 G;
-        geom64_stereo(T, up, vp, hp, G);
-        make_rayf<true>(T, G, href, span, rf);
+        geom_stereo_df(T, uf, vf, hpd, G);
+        make_rayf<true>(T, G, (double)hr, span, rf);
         if (kGrid) rf.X = 0.0f;
         se = (float)G.sin_e;
     }
