@@ -38,10 +38,10 @@ CONFIG = "mid"
 # One launch of the descent kernel on the 4096x4096 workload, from one ncu capture
 # (profiles/dp_task_grid4096.md; None until taken for the current kernel):
 # dram__bytes_read.sum + dram__bytes_write.sum, and the issue counters
-MID_DP_TRAFFIC_BYTES = 91564544 + 94552832
-MID_DP_ISSUE = {"smsp__inst_executed.sum": 13144189368,
-                "smsp__thread_inst_executed.sum": 313331098635,
-                "sm__cycles_elapsed.avg": 30199680.18, "gpu__time_duration.sum_ns": 14594016}
+MID_DP_TRAFFIC_BYTES = 91520000 + 94630400
+MID_DP_ISSUE = {"smsp__inst_executed.sum": 13104574673,
+                "smsp__thread_inst_executed.sum": 312046763948,
+                "sm__cycles_elapsed.avg": 29798239.3, "gpu__time_duration.sum_ns": 14402240}
 SMS, SMSP_PER_SM = 152, 4
 DESCENT_KERNEL = "dp_task_kernel"
 
