@@ -315,7 +315,12 @@ ss_status ss_shadow_backward_ws(const ss_heightfield* hf, const ss_rays* rays, c
  * ss_shadow_forward, giving the same per-ray outputs bit for bit.  The nearest
  * counterpart in the paper is drawing many visible tiles per frame (Sec. 3.3,
  * virtual texturing; Sec. 6.3).  Grid-mode rays (one per texel centre),
- * gnomonic tiles.  params (max_len_m, step_texels, ...) apply to every item. */
+ * gnomonic tiles.  params (max_len_m, step_texels, ...) apply to every item;
+ * zero shape fields take the batch defaults: exact walks in 64 x 64 chunks of
+ * texels (rays_per_thread 128, ray_tile_w 64) with column seeds and services
+ * at 14 idle lanes, light-only walks in runs of 512 (rays_per_thread 16) with
+ * services at 6.  A caller who sets rays_per_thread sets ray_tile_w too
+ * (0 = runs of consecutive texels). */
 typedef struct {
     ss_heightfield hf;     /* device heights; projection SS_PROJ_GNOMONIC       */
     float* mip;            /* device, ss_maxmip_bytes(hf.nx, hf.ny); written    */

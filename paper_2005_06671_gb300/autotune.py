@@ -25,16 +25,16 @@ from .shadow import Batch
 
 SPACE = {
     "block_threads": (128, 256),
-    "rays_per_thread": (4, 8, 16, 32),
+    "rays_per_thread": (8, 16, 32, 64, 128, 256),
     "ray_tile_w": (0, 16, 32, 64),
     "refill_min": (6, 10, 14, 18),
     "leaf_level": (1, 2, 3),
     "strip_len": (0, 1, 6, 10, 16),
 }
-# the starting point: 256 threads, 32 x 64 chunks, services at 14 idle lanes, leaf
-# blocks of 4 samples as warp tasks (64-instance batch on GB300: 350 ms against 392 ms
-# for the single-lane walk's previous default)
-DEFAULT = {"block_threads": 256, "rays_per_thread": 32, "ray_tile_w": 64, "refill_min": 14,
+# the starting point: 256 threads, 64 x 64 chunks (128 rays per lane), services at 14
+# idle lanes, leaf blocks of 4 samples as warp tasks (64-instance batch on GB300:
+# 332 ms against 350 ms for 32 x 64 chunks and 392 ms for the single-lane walk)
+DEFAULT = {"block_threads": 256, "rays_per_thread": 128, "ray_tile_w": 64, "refill_min": 14,
            "leaf_level": 1, "strip_len": 0}
 
 

@@ -293,9 +293,17 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
         return SS_ERR_INVALID_ARG;
     B.block = params->block_threads ? params->block_threads : 256;
     B.count = (params->flags & SS_FLAG_COUNT_SAMPLES) != 0;
-    const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread : 16;
+    // Defaults (64-instance batch on GB300): exact walks take 64 x 64 chunks
+    // (128 rays per lane) with column seeds and services at 14 idle lanes;
+    // light-only walks 32 x 16 runs with services at 6.
+    const bool batch_light = (params->flags & SS_FLAG_LIGHT_ONLY) != 0;
+    const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread
+                        : batch_light              ? 16
+                                                   : 128;
     const int32_t chunk = 32 * rpt;
-    const int32_t tile_w = params->ray_tile_w;
+    const int32_t tile_w = params->ray_tile_w > 0 || params->rays_per_thread > 0 || batch_light
+                               ? params->ray_tile_w
+                               : ss::kBatchSeedW;
     if (tile_w > 0 && chunk % tile_w != 0) return SS_ERR_INVALID_ARG;
     const size_t desc_bytes = ss::align256((size_t)n * sizeof(ss::BatchItemDesc));
     B.image.assign(desc_bytes + (size_t)(n + 1) * sizeof(int64_t), 0);
@@ -345,7 +353,7 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
     B.args.n_items = n;
     B.args.chunk_rays = chunk;
     B.args.kleaf = params->leaf_level < 0 ? 1 : params->leaf_level;   // grid rays
-    B.args.refill_min = params->refill_min > 0 ? params->refill_min : 6;
+    B.args.refill_min = params->refill_min > 0 ? params->refill_min : (batch_light ? 6 : 14);
     B.args.light_only = (params->flags & SS_FLAG_LIGHT_ONLY) ? 1 : 0;
     B.args.strip = params->strip_len > 0 ? params->strip_len
                                          : (B.args.light_only ? 1 : kDefaultStrip);
