@@ -503,21 +503,23 @@ def run_ours(args):
                       "ms_per_step": statistics.mean(fb_ms)}
 
     # ---- end to end through the public API with host buffers.  Every step copies
-    # its heights in from pinned host memory and its light and argmin out; the
-    # copies run on a second stream, so step k's copies overlap the neighbouring
-    # steps' kernels (two sets of device buffers).  Timed from the first copy in
-    # to the last copy out, over all steps.
-    n_e2e = max(3, min(args.steps, 5))
+    # its heights in from pinned host memory and its light and argmin out.  Uploads
+    # and downloads run on two streams of their own, so step k+1's upload and step
+    # k-1's download overlap step k's kernels (two sets of device buffers; a set is
+    # refilled once the step two back has finished reading it, and rewritten once
+    # its results are out).  Timed from the first copy in to the last copy out.
+    n_e2e = max(3, args.steps)
     h_host = torch.from_numpy(h_np).pin_memory()
-    light_host = [torch.empty(n_rays, dtype=torch.float32).pin_memory() for _ in range(n_e2e)]
-    arg_host = [torch.empty(n_rays, dtype=torch.int32).pin_memory() for _ in range(n_e2e)]
+    light_host = [torch.empty(n_rays, dtype=torch.float32).pin_memory() for _ in range(2)]
+    arg_host = [torch.empty(n_rays, dtype=torch.int32).pin_memory() for _ in range(2)]
     sets = []
     for _ in range(2):
         hdev = torch.empty_like(hf.h)
         sets.append(dict(h=hdev, hf=ss.Heightfield(hdev, inst["g"], inst["radius"]),
                          mip=torch.empty_like(mip), light=torch.empty_like(light),
                          argmin=torch.empty_like(argmin)))
-    copy_stream = torch.cuda.Stream(device=dev)
+    h2d_stream = torch.cuda.Stream(device=dev)
+    d2h_stream = torch.cuda.Stream(device=dev)
 
     def e2e_run():
         ev_in = [torch.cuda.Event() for _ in range(n_e2e)]
@@ -525,27 +527,49 @@ def run_ours(args):
         ev_out = [torch.cuda.Event() for _ in range(n_e2e)]
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        copy_stream.wait_stream(stream)
-        t0.record(copy_stream)
+        h2d_stream.wait_stream(stream)
+        d2h_stream.wait_stream(stream)
+        t0.record(h2d_stream)
         for k in range(n_e2e):
             b = sets[k % 2]
-            with torch.cuda.stream(copy_stream):
+            with torch.cuda.stream(h2d_stream):
                 if k >= 2:
-                    copy_stream.wait_event(ev_out[k - 2])   # set b's last results are out
+                    h2d_stream.wait_event(ev_done[k - 2])   # set b's heights are read
                 b["h"].copy_(h_host, non_blocking=True)
-                ev_in[k].record(copy_stream)
+                ev_in[k].record(h2d_stream)
             stream.wait_event(ev_in[k])
+            if k >= 2:
+                stream.wait_event(ev_out[k - 2])            # set b's results are out
             ss.ss_build_maxmip(b["hf"], b["mip"], stream=stream)
             ss.ss_shadow_forward(b["hf"], b["mip"], sun, lmax,
                                  out=dict(light=b["light"], argmin=b["argmin"]),
                                  want_cost=False, stream=stream)
             ev_done[k].record(stream)
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(ev_done[k])
-                light_host[k].copy_(b["light"], non_blocking=True)
-                arg_host[k].copy_(b["argmin"], non_blocking=True)
-                ev_out[k].record(copy_stream)
-        t1.record(copy_stream)
+            with torch.cuda.stream(d2h_stream):
+                d2h_stream.wait_event(ev_done[k])
+                light_host[k % 2].copy_(b["light"], non_blocking=True)
+                arg_host[k % 2].copy_(b["argmin"], non_blocking=True)
+                ev_out[k].record(d2h_stream)
+        t1.record(d2h_stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / n_e2e
+
+    def e2e_serial():
+        """The same steps one at a time on one stream (upload, kernels, download):
+        what the copies cost when nothing overlaps them."""
+        b = sets[0]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(n_e2e):
+            b["h"].copy_(h_host, non_blocking=True)
+            ss.ss_build_maxmip(b["hf"], b["mip"], stream=stream)
+            ss.ss_shadow_forward(b["hf"], b["mip"], sun, lmax,
+                                 out=dict(light=b["light"], argmin=b["argmin"]),
+                                 want_cost=False, stream=stream)
+            light_host[0].copy_(b["light"], non_blocking=True)
+            arg_host[0].copy_(b["argmin"], non_blocking=True)
+        t1.record(stream)
         torch.cuda.synchronize()
         return t0.elapsed_time(t1) / n_e2e
 
@@ -553,14 +577,18 @@ def run_ours(args):
     flush.zero_()
     torch.cuda.synchronize()
     e2e_ms = [e2e_run() for _ in range(2)]
-    ok = bool(torch.equal(torch.from_numpy(timed_light), light_host[-1]))
+    serial_ms = e2e_serial()
+    ok = bool(torch.equal(torch.from_numpy(timed_light), light_host[(n_e2e - 1) % 2]))
     out["e2e"] = {"value": n_rays / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
                   "h2d_bytes_per_step": int(h_host.numel() * 4),
                   "d2h_bytes_per_step": int(light_host[0].numel() * 4 + arg_host[0].numel() * 4),
                   "ms_per_step": statistics.mean(e2e_ms), "steps": n_e2e,
-                  "pipelined": "copies on a second stream overlap the neighbouring steps' "
-                               "kernels; every step copies its own inputs and results",
-                  "same_light_as_timed_step": ok}
+                  "pipelined": "uploads and downloads on their own streams overlap the "
+                               "neighbouring steps' kernels; every step copies its own "
+                               "inputs and results",
+                  "same_light_as_timed_step": ok,
+                  "serial": {"value": n_rays / (serial_ms / 1e3), "ms_per_step": serial_ms,
+                             "note": "one step at a time: upload, kernels, download in order"}}
 
     # ---- batched: 64 uneven tiles in one persistent launch, CUDA-graph replay
     if not args.no_batched:
