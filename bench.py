@@ -435,7 +435,8 @@ def run_ours(args):
                              "frac_rays_differing_from_fp64_build_gt_1e-4":
                                  float((fdiff > 1e-4).float().mean()),
                              "note": "the same algorithm at the paper's float32 arithmetic "
-                                     "(FP64 only for ambiguous tip texels)"}}
+                                     "(float-float for tips within the float32 margin of a "
+                                     "texel edge, FP64 within 1e-6 texel)"}}
 
     # ---- shading epilogue: Sun and Earth lit fractions -> Lambertian irradiance
     from workloads import EARTH_LIGHT
