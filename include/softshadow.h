@@ -174,7 +174,7 @@ typedef struct {
                               the last finished ray of its column (grid rays:
                               columns of the ray rectangle, at most 512 wide,
                               else strips of 10; listed rays: a block's ids
-                              read as 256 columns of consecutive ids).
+                              read as 512 columns of consecutive ids).
                               S in [2, 256]: each lane walks a strip of S
                               neighbouring rays (down a rectangle column, or
                               consecutive ids), seeding from the previous one.

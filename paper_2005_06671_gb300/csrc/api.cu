@@ -228,7 +228,7 @@ ss_status shadow_common(FwdKind kind, const ss_heightfield* hf, const float* mip
     // Defaults (measured on GB300: 4096^2 mid workload, polar view).  The
     // descent (exact and light-only) draws grid rays row by row across 256 x 24
     // ray rectangles, each seeded from the last finished ray of its column
-    // (column seeds, window +-1, leaf level 1); listed rays are read as 256
+    // (column seeds, window +-1, leaf level 1); listed rays are read as 512
     // columns of consecutive ids and drawn the same way (window +-2: adjacent
     // view rays can be several texels apart; leaf level 2).  Uniform stepping
     // draws single rays from row-major runs.

@@ -39,7 +39,7 @@ struct FwdArgs {
 };
 
 constexpr int32_t kColSeedMaxW = 512;    // widest rectangle with a column-seed table
-constexpr int32_t kListSeedCols = 256;   // listed rays: columns of consecutive ids
+constexpr int32_t kListSeedCols = 512;   // listed rays: columns of consecutive ids
 
 struct BwdArgs {
     Tile T;
