@@ -377,8 +377,9 @@ __global__ void __launch_bounds__(kViewBlock) view_hit_kernel(const ViewArgs a) 
 // points near the tile's low edges and failed confirmations finish with
 // halvings to 2^-kViewHalvings of the step, as before.
 __device__ __noinline__ double refine_crossing(const Tile& T, const double C[3], const double d[3],
-                                               double lo_t, double hi_t, double step) {
-    ViewPt lo = view_pt(T, C, d, lo_t), hi = view_pt(T, C, d, hi_t);
+                                               ViewPt lo, double hi_t, double step) {
+    double lo_t = lo.tau;
+    ViewPt hi = view_pt(T, C, d, hi_t);
     const double tol = ldexp(step, -kViewHalvings);
     if (!(lo.in && lo.f > 0.0 && hi.in && hi.f <= 0.0)) {
         // (below()'s and below_fast's roundings disagree at an end): plain halvings
@@ -485,12 +486,12 @@ __global__ void __launch_bounds__(kViewBlock) view_refine_kernel(const ViewArgs 
         pixel_dir(a.cam, p, d);
         const double* C = a.cam.C;
         double hi = (double)hit_k * a.step;
-        bool prev_in = false;
+        // the sample before the hit, evaluated once: its in-tile state decides
+        // whether the crossing is refined, its F starts the refinement
         if (hit_k > 1) {
-            double u, v;
-            below(T, C, d, (double)(hit_k - 1) * a.step, prev_in, u, v);
+            const ViewPt lo = view_pt(T, C, d, (double)(hit_k - 1) * a.step);
+            if (lo.in) hi = refine_crossing(T, C, d, lo, hi, a.step);
         }
-        if (prev_in) hi = refine_crossing(T, C, d, (double)(hit_k - 1) * a.step, hi, a.step);
         const double xh[3] = { C[0] + hi * d[0], C[1] + hi * d[1], C[2] + hi * d[2] };
         double hu, hv;
         // the point lies between two samples of the tile: it has an image
