@@ -293,9 +293,10 @@ ss_status batch_prepare(const ss_batch_item* items, int32_t n, const ss_params* 
         return SS_ERR_INVALID_ARG;
     B.block = params->block_threads ? params->block_threads : 256;
     B.count = (params->flags & SS_FLAG_COUNT_SAMPLES) != 0;
-    // Defaults (64-instance batch on GB300): exact walks take 64 x 64 chunks
-    // (128 rays per lane) with column seeds and services at 14 idle lanes;
-    // light-only walks 32 x 16 runs with services at 6.
+    // Defaults (64-instance batch on GB300): exact walks take 64 x 64-texel
+    // chunks (128 rays per lane) with column seeds and services at 14 idle
+    // lanes; light-only walks runs of 512 texels (16 rays per lane) with
+    // services at 6.
     const bool batch_light = (params->flags & SS_FLAG_LIGHT_ONLY) != 0;
     const int32_t rpt = params->rays_per_thread > 0 ? params->rays_per_thread
                         : batch_light              ? 16

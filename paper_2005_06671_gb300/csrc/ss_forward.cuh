@@ -501,9 +501,9 @@ __global__ void __launch_bounds__(256, SS_FWD_MIN_BLOCKS) dp_task_kernel(const F
 // The task descent (ss_task.cuh) serves exact walks with column seeds: grid
 // rays in rectangles (leaf blocks of <= 4 samples on gnomonic tiles, <= 8 on
 // stereographic ones), listed rays in runs (<= 8).  (Polar view, 6.0 M rays on
-// the 16384^2 stereographic tile: 28.5 ms against 37.5 ms for the single-lane
-// walk, once the float32 range search took the FP64 crossings out of the
-// setup; with them the tasks had measured slower, 70 against 65 ms.)
+// the 16384^2 stereographic tile, 32 rays per lane: 28.5 ms against 37.5 ms for
+// the single-lane walk, once the float32 range search took the FP64 crossings
+// out of the setup; with them the tasks had measured slower, 70 against 65 ms.)
 inline bool use_task_descent(const FwdArgs& a, bool grid, bool stereo, bool light) {
     return !light && a.colseed && (!grid || a.tile_w > 0) &&
            a.kleaf <= (grid && !stereo ? 1 : 2) && !(a.flags & 0x10u);   // SS_FLAG_LANE_LEAVES
