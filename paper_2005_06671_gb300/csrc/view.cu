@@ -23,9 +23,9 @@
 // a scatter), so the ray list is deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include <cmath>
-#include <stdint.h>
 
 #include "ss_launch.h"
 
